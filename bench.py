@@ -1,0 +1,429 @@
+"""Benchmark: markers/s of one MLS transfer step (marker prep + build + interpolate + spread).
+
+Default workload: 2000 ellipsoids of 1280 markers each (2.56 M markers) in a
+uniform periodic 512^3 grid, single precision, exact-MLS (the fast-MLS step
+is timed alongside and reported under "fast").  Inputs are synthetic and
+resident in HBM before timing; L2 is flushed (256 MiB write) between timed
+steps, outside the timed events.  One JSON line on stdout (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c3|c1] [--method exact|fast]
+
+With N > 1 (torchrun) every rank runs its own copy of the workload on its
+GPU (independent bodies, no data-path collective: weak scaling); value is
+the markers of all ranks over the slowest rank's time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "markers/s (build+interp+spread) and HBM roofline fraction at stated err vs FP64"
+WORKLOAD_TEXT = {
+    "c1": "1 level-4 icosphere (5120 markers), R=0.25, periodic 64^3 grid, float64",
+    "c2": "2000 ellipsoids x 1280 markers (2.56M), periodic uniform 512^3 grid, float32",
+    "c3": "10^4 deformed icospheres (50/50 1280/5120 markers, 32M), 1024^3 grid tanh-stretched in z, float32",
+}
+
+# Algorithmic bytes per marker of each kernel (float32 path; u_cells = distinct
+# touched cells per marker, measured).  See DESIGN.md, "Roofline".
+def algorithmic_bytes(kernel, rs, u_cells, verts_per_marker):
+    return {
+        "marker_prep": 12 + 3 * rs * verts_per_marker + 4 * rs,
+        "locate": 3 * rs + 8,
+        "scatter": 12,
+        "build_exact": 4 + 4 * rs + 27 * rs + rs + 4,
+        "build_fast": 4 + 4 * rs + 27 * rs + rs + 4,
+        "interp": 27 * rs + 8 + 3 * rs * u_cells + 3 * rs,
+        "spread": 27 * rs + rs + 8 + 3 * rs + 6 * rs * u_cells,
+    }.get(kernel)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    p.add_argument("--method", default="exact", choices=["exact", "fast"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sample-bodies", type=int, default=160, help="bodies in the CPU oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name):
+    from workloads import make_workload
+    return make_workload(name)
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+ORACLE_CHILD = r"""
+import json, os, sys, time
+sys.path.insert(0, os.environ["MLS_ROOT"])
+import numpy as np
+import oracle
+from workloads import make_workload
+from workloads.fields import field_at_cells_np
+args = json.loads(sys.argv[1])
+w = make_workload(args["workload"])
+g = oracle.Grid(w.faces, w.periodic)
+b0, b1 = args["bodies"]
+f0, f1 = int(w.body_faces[b0]), int(w.body_faces[b1])
+tri = w.tri[f0:f1]
+real = w.real
+V = w.vertices.astype(np.float32 if real == "f32" else np.float64)
+F = w.forces()[:, f0:f1].astype(V.dtype)
+times = []
+for rep in range(args["reps"]):
+    t0 = time.perf_counter()
+    x, area = oracle.marker_prep(V, tri, real)
+    tr = oracle.shape_exact(g, x, 1.0) if args["method"] == "exact" else oracle.shape_fast(g, x, 1.0, 9)
+    c = oracle.forcing_scale(tr, area)
+    ix, iy, iz = tr.sup.idx
+    usup = field_at_cells_np(w.modes, w.faces, ix.ravel(), iy.ravel(), iz.ravel()).reshape((3,) + ix.shape)
+    if real == "f32":
+        usup = usup.astype(np.float32).astype(np.float64)
+    U = np.einsum("mk,cmk->cm", tr.phi, usup)
+    sp = oracle.spread(tr, c, F, g.n)
+    times.append(time.perf_counter() - t0)
+keep = slice(0, min(2000, f1 - f0))
+np.savez(args["out"], phi=tr.phi[keep], U=U[:, keep], c=c[keep])
+print(json.dumps({"markers": int(f1 - f0), "times": times}))
+"""
+
+
+def run_oracle_sample(name, method, bodies, reps, out):
+    env = dict(os.environ)
+    env["MLS_ROOT"] = ROOT
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    args = json.dumps({"workload": name, "method": method, "bodies": bodies, "reps": reps, "out": out})
+    r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, args], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [v.strip() for v in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(p))
+    except Exception:
+        return None
+    ent = data.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1805_01113_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1805_01113_gb300 import build_ext
+    build_ext.build()
+    from paper_1805_01113_gb300 import api
+    from workloads.fields import field_full_torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(a.workload)
+    real = w.real
+    tdt = torch.float32 if real == "f32" else torch.float64
+    rs = 4 if real == "f32" else 8
+    M = w.n_markers
+    ctx = api.Context(w.faces, w.periodic, real=real)
+    V_host = torch.as_tensor(w.vertices.astype(np.float32 if real == "f32" else np.float64)).pin_memory()
+    F_host = torch.as_tensor(w.forces().astype(np.float32 if real == "f32" else np.float64)).pin_memory()
+    V = V_host.to(dev)
+    tri = torch.as_tensor(w.tri, device=dev)
+    F = F_host.to(dev)
+    u = field_full_torch(w.modes, w.faces, tdt, dev)
+    f = torch.zeros_like(u)
+    x = torch.empty((3, M), dtype=tdt, device=dev)
+    area = torch.empty((M,), dtype=tdt, device=dev)
+    U = torch.empty((3, M), dtype=tdt, device=dev)
+    T = ctx.transfer(M)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(method):
+        ctx.marker_prep(V, tri, x, area)
+        ctx.build_transfer(T, x, area, method)
+        ctx.interpolate(T, u, U)
+        ctx.spread(T, F, f)
+
+    # distinct touched cells per marker (u_cells) from one spread into a zero field
+    step(a.method)
+    st = ctx.status(T)
+    if st["dropped"]:
+        raise RuntimeError(f"{st['dropped']} markers dropped")
+    f.zero_()
+    ctx.spread(T, F, f)
+    touched = int(torch.count_nonzero(f[0]).item())
+    u_cells = touched / M
+
+    def timed(method, steps, warmup, per_kernel):
+        for _ in range(warmup):
+            step(method)
+        torch.cuda.synchronize()
+        if per_kernel:
+            ctx.read_timing()
+            ctx.timing(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record(stream)
+            step(method)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        kt = ctx.read_timing() if per_kernel else {}
+        ctx.timing(False)
+        return ms, kt
+
+    # headline: plain timed region (no per-kernel events), clocks sampled during it
+    clk = ClockSampler(local)
+    clk.start()
+    ms, _ = timed(a.method, a.steps, a.warmup, False)
+    clocks = clk.stop()
+    total_ms = sum(ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * M * a.steps / (total_ms / 1e3)
+
+    # per-kernel pass (events around each kernel on the launching stream)
+    ms_k, kt = timed(a.method, a.steps, 2, True)
+    launches = sum(n for k, (n, _) in kt.items() if k != "bin_reset")
+    per_launch = {k: tot / n for k, (n, tot) in kt.items() if n}
+    dom = max((k for k in per_launch if k != "bin_reset"), key=lambda k: kt[k][1])
+    pk, pk_src = peaks()
+    vpm = len(w.vertices) / M
+    byts = {k: algorithmic_bytes(k, rs, u_cells, vpm) for k in per_launch}
+    ach = byts[dom] * M / (per_launch[dom] / 1e3) / 1e9 if byts.get(dom) else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": (ach / pk["hbm_gbs"]) if ach else None, "peak_source": pk_src,
+            "algorithmic_bytes_per_launch": byts[dom] * M if byts.get(dom) else None,
+            "traffic": traffic_for(dom)}
+    kernels = {k: {"ms_per_launch": round(per_launch[k], 5), "launches_per_step": kt[k][0] / a.steps,
+                   "gbs": (round(byts[k] * M / (per_launch[k] / 1e3) / 1e9, 1) if byts.get(k) else None)}
+               for k in per_launch}
+
+    # the other method, same workload (reported, not the headline)
+    other = "fast" if a.method == "exact" else "exact"
+    ms_o, _ = timed(other, max(3, a.steps // 2), 3, False)
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # vertices and forces from pinned memory, D2H of the marker velocities
+    e2e = None
+    if not a.no_e2e:
+        U_host = torch.empty((3, M), dtype=tdt).pin_memory()
+
+        def e2e_step():
+            V.copy_(V_host, non_blocking=True)
+            F.copy_(F_host, non_blocking=True)
+            step(a.method)
+            U_host.copy_(U, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = []
+        for _ in range(a.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            te.append(time.perf_counter() - t0)
+        e2e = {"value": M * world / statistics.mean(te), "unit": "markers/s",
+               "h2d_bytes_per_step": V_host.numel() * V_host.element_size() + F_host.numel() * F_host.element_size(),
+               "d2h_bytes_per_step": U_host.numel() * U_host.element_size(),
+               "ms_per_step": 1e3 * statistics.mean(te)}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only), plus its error check
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        nb = min(a.sample_bodies, len(w.body_faces) - 1)
+        with tempfile.TemporaryDirectory() as td:
+            out = os.path.join(td, "s.npz")
+            r = run_oracle_sample(a.workload, a.method, [0, nb], 1, out)
+            ref = np.load(out)
+            k = ref["phi"].shape[0]
+            v = ctx.view(T)
+            inv = torch.empty(M, dtype=torch.long, device=dev)
+            inv[v["perm"].long()] = torch.arange(M, device=dev)
+            ctx.marker_prep(V, tri, x, area)
+            ctx.build_transfer(T, x, area, a.method)
+            ctx.interpolate(T, u, U)
+            v = ctx.view(T)
+            inv[v["perm"].long()] = torch.arange(M, device=dev)
+            phi_g = v["phi"][:, inv[:k]].double().cpu().numpy().T
+            U_g = U[:, :k].double().cpu().numpy()
+            err = {"phi_max_rel": float(np.max(np.abs(phi_g - ref["phi"])) / np.max(np.abs(ref["phi"]))),
+                   "U_max_rel": float(np.max(np.abs(U_g - ref["U"])) / np.max(np.abs(ref["U"]))),
+                   "U_rms_rel": float(np.sqrt(np.mean((U_g - ref["U"]) ** 2)) / np.sqrt(np.mean(ref["U"] ** 2))),
+                   "markers_compared": int(k)}
+        cpu = {"value": r["markers"] / min(r["times"]), "unit": "markers/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {nb} bodies ({r['markers']} markers) of the same workload, prep+{a.method} build"
+                         f"+interp+spread, numpy float64, single thread",
+               "err_vs_fp64_oracle": err}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "markers/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": real, "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[a.workload], "markers_per_gpu": M, "method": a.method,
+                   "grid": list(w.n), "l2": "flushed by a 256 MiB write before every timed step",
+                   "step": "marker_prep + build_transfer + interpolate + spread",
+                   "touched_cells_per_marker": round(u_cells, 4)},
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+        other: {"value": M * world / (statistics.mean(ms_o) / 1e3), "ms_per_step": statistics.mean(ms_o)},
+        "e2e": e2e, "clocks": clocks, "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    w = workload(a.workload)
+    nb = 20
+    times = []
+    steps = max(1, a.steps)
+    for s in range(a.warmup + steps):
+        b0 = (s * nb) % (len(w.body_faces) - 1 - nb)
+        with tempfile.TemporaryDirectory() as td:
+            r = run_oracle_sample(a.workload, a.method, [b0, b0 + nb], 1, os.path.join(td, "s.npz"))
+        if s >= a.warmup:
+            times.append(r["times"][0] / r["markers"])
+    per_marker = statistics.mean(times)
+    value = 1.0 / per_marker
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "markers/s", "n_gpus": world,
+            "steps": steps, "warmup": a.warmup, "ms_per_step": per_marker * w.n_markers * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[a.workload], "method": a.method,
+                       "sample": f"{nb} bodies per step, extrapolated per marker"},
+            "cpu_baseline": {"value": value, "unit": "markers/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{nb} bodies of the workload per step, numpy float64, single thread"},
+            "e2e": {"value": value, "unit": "markers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if a.impl == "ours" else "gloo"
+        if a.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    try:
+        if a.impl == "reference":
+            run_reference(a, rank, world)
+        else:
+            run_ours(a, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * mls.h -- C ABI of the GB300 moving-least-squares (MLS) transfer library.
+ *
+ * The library builds MLS shape functions for Lagrangian markers (centroids of
+ * surface triangles) immersed in an Eulerian grid and uses them to move data
+ * between the two meshes, following Section 2 of Spandan, Lohse, de Tullio &
+ * Verzicco, "A fast moving least squares approximation with adaptive
+ * Lagrangian mesh refinement for large scale immersed boundary simulations"
+ * (J. Comput. Phys.; arXiv:1805.01113):
+ *
+ *   build      Phi^T(x_l) = p^T(x_l) A^-1(x_l) B(x_l)          Eqs. 3, 4, 6
+ *              (exact-MLS), or the Shepard blend of tabulated
+ *              exact shape functions                            Eqs. 9, 10
+ *              plus the spreading scale c_l                      Eqs. 7, 8
+ *   interpolate U_l = sum_k phi_k^l u_k                          text after Eq. 6
+ *   spread      f_k += sum_l c_l phi_k^l F_l                     text after Eq. 7
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status (MLS_OK = 0, codes below).  A non-zero
+ *     code leaves outputs unspecified; mls_last_error() gives a message for the
+ *     calling thread.
+ *   - Pointers marked "device" point to CUDA device memory owned by the
+ *     caller; the library never frees them.  Pointers marked "host" are read
+ *     during the call only.  Handles (mls_ctx, mls_transfer) are owned by the
+ *     library and released by their destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it unless stated otherwise; the
+ *     caller orders its own reads of outputs after the stream.
+ *   - "real" is the context's arithmetic type: double for MLS_F64, float for
+ *     MLS_F32.  "field" is the storage type of Eulerian fields: double,
+ *     float or bfloat16 (MLS_BF16).
+ *   - Marker arrays are structure-of-arrays: x[3][M] (x, then y, then z), one
+ *     row of M values per component; same for U and F.  Eulerian fields are
+ *     u[3][nz][ny][nx], x fastest.
+ *   - Support node order: k = 9*(a_z+1) + 3*(a_y+1) + (a_x+1) for offsets
+ *     a in {-1,0,1}^3 around the home cell (the cell with
+ *     face_i <= x < face_{i+1} on every axis).
+ */
+#ifndef MLS_GB300_H
+#define MLS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MLS_OK                0
+#define MLS_ERR_INVALID_ARG   1  /* bad pointer, size, option or handle combination */
+#define MLS_ERR_CAPACITY      2  /* more markers than the transfer handle was created for */
+#define MLS_ERR_UNSUPPORTED   3  /* valid request this build does not implement */
+#define MLS_ERR_CUDA          4  /* a CUDA runtime call failed (see mls_last_error) */
+#define MLS_ERR_OUT_OF_DOMAIN 5  /* mls_transfer_status: some markers were dropped */
+
+/* ---- methods and number types ---------------------------------------- */
+#define MLS_EXACT 0  /* exact-MLS, Eqs. 3-6 */
+#define MLS_FAST  1  /* fast-MLS, Eqs. 9-10 */
+
+#define MLS_F64  0
+#define MLS_F32  1
+#define MLS_BF16 2
+
+typedef struct mls_ctx mls_ctx;
+typedef struct mls_transfer mls_transfer;
+
+/* Eulerian grid (Section 2, Fig. 1a): per-axis face coordinates.  Cell i of
+ * axis d spans [faces[d][i], faces[d][i+1]); its centre is a support node and
+ * its width enters Eqs. 7-8.  Axis order is x, y, z. */
+typedef struct {
+  int32_t n[3];              /* cells per axis, >= 3; n[0]*n[1]*n[2] < 2^31 */
+  int32_t periodic[3];       /* 1: supports wrap around; 0: walled, a marker
+                                whose support would leave the grid is dropped */
+  const double* faces[3];    /* host, n[d]+1 strictly increasing values */
+} mls_grid;
+
+typedef struct {
+  int32_t real;          /* MLS_F64 or MLS_F32 (default MLS_F32) */
+  int32_t field;         /* MLS_F64 (needs real = MLS_F64), MLS_F32 or MLS_BF16 */
+  double eps;            /* Gaussian weight W = exp(-r^2/eps^2), r in home-cell
+                            widths per axis (reading of the text after Eq. 2); default 1 */
+  int32_t n_sub;         /* fast-MLS sub-Eulerian points per axis (Fig. 1b/1c), 3..33, default 9 */
+  int32_t brick_log2[3]; /* spreading tile of 2^b home cells per axis, 1..5 each, default 3 */
+  double cond_max;       /* MLS_F32 only: re-solve Eq. 6 in double when cond_1(A) exceeds this; <= 0 disables; default 1e6 */
+  int32_t refine;        /* MLS_F32 only: iterative-refinement steps of the 4x4 solve, 0..2, default 1 */
+} mls_options;
+
+/* Device views into a built transfer (borrowed; valid until the next build on
+ * the handle or its destruction).  Markers are stored in "tile order", a
+ * permutation of the caller's order that groups markers by spreading tile. */
+typedef struct {
+  int64_t M;             /* markers in the last build */
+  const void* phi;       /* device, real[27][capacity]: phi[k][j] for stored marker j (Eq. 6 / Eq. 9) */
+  const void* c;         /* device, real[capacity]: c_l of Eq. 8 (0 for dropped markers) */
+  const int32_t* home;   /* device, int32[capacity]: (iz*ny + iy)*nx + ix of the home cell, -1 if dropped */
+  const int32_t* perm;   /* device, int32[capacity]: caller's marker index of stored marker j */
+  int64_t capacity;
+} mls_transfer_arrays;
+
+/* Device-side counters of the last build (read with mls_transfer_status). */
+typedef struct {
+  int64_t dropped;       /* markers outside the grid, non-finite, or with a support leaving a walled axis */
+  int64_t nonfinite;     /* of which: non-finite position or area */
+  int64_t refined_fp64;  /* MLS_F32 exact builds re-solved in double (cond_1(A) > cond_max) */
+} mls_status;
+
+typedef struct {
+  const char* name;      /* kernel name (static string) */
+  int64_t launches;
+  double total_ms;       /* sum of CUDA-event durations on the launching stream */
+} mls_kernel_time;
+
+/* Fill `opt` with the defaults listed above.  Never fails for non-NULL opt. */
+int mls_options_default(mls_options* opt);
+
+/* Create a context for one grid and option set on the current CUDA device.
+ * Copies the grid to the device (allocates; synchronous).  Fails with
+ * MLS_ERR_INVALID_ARG on non-increasing faces, n < 3, or bad options, and
+ * with MLS_ERR_UNSUPPORTED when fast-MLS tables would be needed for more than
+ * one non-uniform axis (checked lazily at the first MLS_FAST build). */
+int mls_create(const mls_grid* grid, const mls_options* opt, mls_ctx** out);
+int mls_destroy(mls_ctx* ctx);
+
+/* Allocate a transfer handle for up to `capacity` markers (synchronous
+ * allocation of phi, c, home, perm and the tile-sort workspace).  Builds
+ * into it allocate nothing. */
+int mls_transfer_create(mls_ctx* ctx, int64_t capacity, mls_transfer** out);
+int mls_transfer_destroy(mls_transfer* T);
+
+/* Marker preparation (Section 3, Fig. 5a; Eq. 7): for triangle t with
+ * vertices V1, V2, V3 = vertices[tri[t][0..2]], write the centroid
+ * x[:, t] = ((V1 + V2) + V3)/3 and the area area[t] = |(V2-V1)x(V3-V1)|/2,
+ * evaluated in the context's real type in exactly that operation order
+ * (IEEE round-to-nearest, no contraction).
+ *   vertices  device, real[n_vertices][3] (interleaved x, y, z)
+ *   tri       device, int32[n_tri][3]
+ *   x         device, real[3][n_tri]     area  device, real[n_tri]
+ * A triangle with a vertex index outside [0, n_vertices) gets a NaN centroid
+ * (the next build drops and counts it). */
+int mls_marker_prep(mls_ctx* ctx, const void* vertices, int64_t n_vertices,
+                    const int32_t* tri, int64_t n_tri, void* x, void* area, void* stream);
+
+/* Build the transfer functions of M markers into T (Section 2).
+ *   x     device, real[3][M] marker positions; area device, real[M] (A_l, Eq. 7)
+ *   method MLS_EXACT (Eqs. 3-6) or MLS_FAST (Eqs. 9-10; the first fast build
+ *          on a context tabulates exact shape functions on the sub-Eulerian
+ *          mesh, once, on `stream`).
+ * Markers are sorted into spreading tiles; phi, c, home and perm are written
+ * in that order (see mls_transfer_arrays).  Dropped markers get phi = 0,
+ * c = 0, home = -1 and are counted in mls_status.
+ * Errors: MLS_ERR_CAPACITY if M > capacity; MLS_ERR_INVALID_ARG on NULL
+ * pointers with M > 0 or an unknown method. */
+int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area,
+                       int64_t M, int32_t method, void* stream);
+
+/* Euler-to-Lagrange interpolation U_l = sum_k phi_k^l u_k (text after Eq. 6)
+ * for the 3 components, accumulated in the real type.
+ *   u  device, field[3][nz][ny][nx]     U  device, real[3][M] (caller's marker order)
+ * Dropped markers get U = 0. */
+int mls_interpolate(mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, void* stream);
+
+/* Lagrange-to-Euler spreading f_k += sum_l c_l phi_k^l F_l (text after
+ * Eq. 7).  Accumulates into f (the caller zeroes it when it wants a fresh
+ * field); partial sums are formed per spreading tile in the real type and
+ * added to f with atomic adds, so the summation order is not deterministic.
+ *   F  device, real[3][M] (caller's marker order)   f  device, field[3][nz][ny][nx] */
+int mls_spread(mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, void* stream);
+
+/* Borrowed device views of the last build (no synchronisation). */
+int mls_transfer_view(const mls_transfer* T, mls_transfer_arrays* out);
+
+/* Synchronise `stream`, then read the counters of the last build.  Returns
+ * MLS_OK, or MLS_ERR_OUT_OF_DOMAIN when out->dropped > 0. */
+int mls_transfer_status(const mls_transfer* T, void* stream, mls_status* out);
+
+/* Fast-MLS table of the context (built on demand on `stream`):
+ * real[n_classes][n_sub^3][27], sub-node order s = (s_z*n + s_y)*n + s_x,
+ * class = home index along the one non-uniform axis (0 when all are uniform). */
+int mls_fast_table(mls_ctx* ctx, void* stream, const void** table, int64_t* n_classes, int32_t* n_sub);
+
+/* Per-kernel CUDA-event timing on the launching stream (off by default).
+ * mls_timing_read synchronises the device, returns up to `max` accumulated
+ * records in `out`, their count in `n`, and resets the accumulators. */
+int mls_timing_enable(mls_ctx* ctx, int32_t on);
+int mls_timing_read(mls_ctx* ctx, mls_kernel_time* out, int32_t max, int32_t* n);
+
+const char* mls_strerror(int32_t code);
+const char* mls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLS_GB300_H */

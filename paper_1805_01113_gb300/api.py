@@ -1,0 +1,190 @@
+"""PyTorch-facing wrapper of the C ABI: tensors in, device pointers and streams out.
+
+Only marshalling happens here (shape/dtype/device checks, pointer and stream
+extraction); every step of the path runs in libmls_gb300.so kernels.
+"""
+
+import ctypes as C
+
+import torch
+
+from . import binding as B
+
+DTYPES = {"f64": (B.MLS_F64, torch.float64), "f32": (B.MLS_F32, torch.float32),
+          "bf16": (B.MLS_BF16, torch.bfloat16)}
+METHODS = {"exact": B.MLS_EXACT, "fast": B.MLS_FAST}
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, name, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory via __cuda_array_interface__."""
+
+    _TYPESTR = {torch.float64: "<f8", torch.float32: "<f4", torch.int32: "<i4"}
+
+    def __init__(self, ptr, shape, dtype, strides=None):
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": self._TYPESTR[dtype], "data": (int(ptr or 0), False),
+            "version": 3, "strides": strides,
+        }
+
+
+class Transfer:
+    """A transfer handle (library-owned phi, c, home, perm for up to `capacity` markers)."""
+
+    def __init__(self, ctx, capacity):
+        self.ctx = ctx
+        self.capacity = int(capacity)
+        h = C.c_void_p()
+        B.check(ctx.lib.mls_transfer_create(ctx.handle, self.capacity, C.byref(h)), "mls_transfer_create")
+        self.handle = h
+        self.M = 0
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.mls_transfer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """One grid + option set (mls_create)."""
+
+    def __init__(self, faces, periodic, real="f32", field=None, eps=1.0, n_sub=9, brick_log2=(3, 3, 3),
+                 cond_max=1e6, refine=1):
+        self.lib = B.load()
+        field = field or real
+        self.real_code, self.real_t = DTYPES[real]
+        self.field_code, self.field_t = DTYPES[field]
+        self.n = tuple(len(f) - 1 for f in faces)
+        g = B.mls_grid()
+        self._faces = [(C.c_double * len(f))(*[float(v) for v in f]) for f in faces]
+        for d in range(3):
+            g.n[d] = self.n[d]
+            g.periodic[d] = 1 if periodic[d] else 0
+            g.faces[d] = C.cast(self._faces[d], C.POINTER(C.c_double))
+        o = B.mls_options()
+        self.lib.mls_options_default(C.byref(o))
+        o.real, o.field, o.eps, o.n_sub = self.real_code, self.field_code, float(eps), int(n_sub)
+        for d in range(3):
+            o.brick_log2[d] = int(brick_log2[d])
+        o.cond_max, o.refine = float(cond_max), int(refine)
+        self.options = o
+        h = C.c_void_p()
+        B.check(self.lib.mls_create(C.byref(g), C.byref(o), C.byref(h)), "mls_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.lib.mls_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points -------------------------------------------------------
+    def transfer(self, capacity):
+        return Transfer(self, capacity)
+
+    def marker_prep(self, vertices, tri, x=None, area=None, stream=None):
+        nt = tri.shape[0]
+        _check_tensor(vertices, "vertices", self.real_t)
+        _check_tensor(tri, "tri", torch.int32, (nt, 3))
+        if vertices.dim() != 2 or vertices.shape[1] != 3:
+            raise ValueError("vertices must be (n_vertices, 3)")
+        if x is None:
+            x = torch.empty((3, nt), dtype=self.real_t, device=vertices.device)
+        if area is None:
+            area = torch.empty((nt,), dtype=self.real_t, device=vertices.device)
+        _check_tensor(x, "x", self.real_t, (3, nt))
+        _check_tensor(area, "area", self.real_t, (nt,))
+        B.check(self.lib.mls_marker_prep(self.handle, _ptr(vertices), vertices.shape[0], _ptr(tri), nt,
+                                         _ptr(x), _ptr(area), _stream(stream)), "mls_marker_prep")
+        return x, area
+
+    def build_transfer(self, T, x, area, method="exact", stream=None):
+        M = x.shape[1]
+        _check_tensor(x, "x", self.real_t, (3, M))
+        _check_tensor(area, "area", self.real_t, (M,))
+        B.check(self.lib.mls_build_transfer(self.handle, T.handle, _ptr(x), _ptr(area), M, METHODS[method],
+                                            _stream(stream)), "mls_build_transfer")
+        T.M = M
+        return T
+
+    def interpolate(self, T, u, U=None, stream=None):
+        _check_tensor(u, "u", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        if U is None:
+            U = torch.empty((3, T.M), dtype=self.real_t, device=u.device)
+        _check_tensor(U, "U", self.real_t, (3, T.M))
+        B.check(self.lib.mls_interpolate(self.handle, T.handle, _ptr(u), _ptr(U), _stream(stream)),
+                "mls_interpolate")
+        return U
+
+    def spread(self, T, F, f, stream=None):
+        _check_tensor(F, "F", self.real_t, (3, T.M))
+        _check_tensor(f, "f", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        B.check(self.lib.mls_spread(self.handle, T.handle, _ptr(F), _ptr(f), _stream(stream)), "mls_spread")
+        return f
+
+    def status(self, T, stream=None):
+        s = B.mls_status()
+        rc = self.lib.mls_transfer_status(T.handle, _stream(stream), C.byref(s))
+        if rc not in (B.MLS_OK, B.MLS_ERR_OUT_OF_DOMAIN):
+            B.check(rc, "mls_transfer_status")
+        return {"code": rc, "dropped": s.dropped, "nonfinite": s.nonfinite, "refined_fp64": s.refined_fp64}
+
+    def view(self, T):
+        """Zero-copy torch views of the last build: phi (27, M), c (M,), home (M,), perm (M,)."""
+        a = B.mls_transfer_arrays()
+        B.check(self.lib.mls_transfer_view(T.handle, C.byref(a)), "mls_transfer_view")
+        M, cap = a.M, a.capacity
+        es = torch.empty((), dtype=self.real_t).element_size()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        phi = torch.as_tensor(_DeviceArray(a.phi, (27, M), self.real_t, (cap * es, es)), device=dev)
+        c = torch.as_tensor(_DeviceArray(a.c, (M,), self.real_t), device=dev)
+        home = torch.as_tensor(_DeviceArray(a.home, (M,), torch.int32), device=dev)
+        perm = torch.as_tensor(_DeviceArray(a.perm, (M,), torch.int32), device=dev)
+        return {"phi": phi, "c": c, "home": home, "perm": perm}
+
+    def fast_table(self, stream=None):
+        p, nc, ns = C.c_void_p(), C.c_int64(), C.c_int32()
+        B.check(self.lib.mls_fast_table(self.handle, _stream(stream), C.byref(p), C.byref(nc), C.byref(ns)),
+                "mls_fast_table")
+        s3 = ns.value ** 3
+        dev = torch.device("cuda", torch.cuda.current_device())
+        return torch.as_tensor(_DeviceArray(p.value, (nc.value, s3, 27), self.real_t), device=dev)
+
+    def timing(self, on=True):
+        B.check(self.lib.mls_timing_enable(self.handle, 1 if on else 0), "mls_timing_enable")
+
+    def read_timing(self):
+        buf = (B.mls_kernel_time * 64)()
+        n = C.c_int32()
+        B.check(self.lib.mls_timing_read(self.handle, buf, 64, C.byref(n)), "mls_timing_read")
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}

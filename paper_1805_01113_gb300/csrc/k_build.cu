@@ -1,0 +1,254 @@
+// Shape-function builds: exact-MLS (Eqs. 3-6), the fast-MLS table of exact
+// shape functions on the sub-Eulerian mesh, and fast-MLS (Eqs. 9-10).
+// One thread per marker, markers visited in tile order (perm), so phi[k][j],
+// c[j] and home[j] are written with unit stride across a warp.
+#include "mls_host.h"
+
+namespace mls {
+
+template <typename R>
+struct BuildArgs {
+  Grid<R> g;
+  Grid<double> gd;       // double-precision grid for the conditioning fallback
+  const R* x;
+  const R* area;
+  const int32_t* perm;
+  int64_t M, cap;
+  R* phi;
+  R* c;
+  int32_t* home;
+  unsigned long long* status;
+  R inv_eps2;
+  double inv_eps2_d;
+  int refine;
+  double cond_max;
+  // fast-MLS
+  const R* table;
+  int class_axis;
+  int n_sub;
+};
+
+// Shared prologue: fetch marker perm[j], locate its home cell, and build the
+// per-axis node geometry.  Dropped markers get phi = 0, c = 0, home = -1.
+template <typename R>
+__device__ __forceinline__ bool marker_setup(const BuildArgs<R>& a, int64_t j, int h[3], R p[3],
+                                             AxisNodes<R> s[3], R& ar) {
+  const int64_t m = a.perm[j];
+  p[0] = a.x[m];
+  p[1] = a.x[a.M + m];
+  p[2] = a.x[2 * a.M + m];
+  ar = a.area[m];
+  bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(ar);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    h[d] = locate_axis(a.g.ax[d], p[d]);
+    ok = ok && support_ok(a.g.ax[d], h[d]);
+  }
+  if (!ok) {
+#pragma unroll
+    for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = R(0);
+    a.c[j] = R(0);
+    a.home[j] = -1;
+    return false;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) s[d] = axis_nodes(a.g.ax[d], h[d], p[d]);
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ void marker_store(const BuildArgs<R>& a, int64_t j, const int h[3],
+                                             const AxisNodes<R> s[3], const R phi[27], R ar) {
+#pragma unroll
+  for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = phi[k];
+  a.c[j] = scale_factor(s, phi, ar);
+  a.home[j] = (h[2] * a.g.ax[1].n + h[1]) * a.g.ax[0].n + h[0];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_build_exact(BuildArgs<R> a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.M) return;
+  int h[3];
+  R p[3], ar;
+  AxisNodes<R> s[3];
+  if (!marker_setup(a, j, h, p, s, ar)) return;
+  R phi[27];
+  R cond = R(0);
+  const bool want_cond = sizeof(R) == 4 && a.cond_max > 0.0;
+  bool good = shape_exact<R>(s, a.inv_eps2, a.refine, phi, want_cond ? &cond : nullptr);
+  if (sizeof(R) == 4 && (!good || (want_cond && (double)cond > a.cond_max))) {
+    // Ill-conditioned (or not numerically SPD) in single precision: redo the
+    // marker in double and round the result.
+    AxisNodes<double> sd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sd[d] = axis_nodes(a.gd.ax[d], h[d], (double)p[d]);
+    double phid[27];
+    good = shape_exact<double>(sd, a.inv_eps2_d, 0, phid, nullptr);
+#pragma unroll
+    for (int k = 0; k < 27; ++k) phi[k] = (R)phid[k];
+    atomicAdd(&a.status[2], 1ULL);
+  }
+  if (!good) {
+#pragma unroll
+    for (int k = 0; k < 27; ++k) phi[k] = R(0);
+  }
+  marker_store(a, j, h, s, phi, ar);
+}
+
+// Fast-MLS: the marker's position in its home cell picks the enclosing
+// sub-cell of the n^3 sub-Eulerian mesh; the shape function is the Shepard
+// blend of the 8 corner rows of the table, alpha_i proportional to 1/d_i^2
+// (Eq. 10), evaluated as alpha_i = prod_{j!=i} d_j^2 / sum_i prod_{j!=i} d_j^2
+// which equals it and stays finite when the marker sits on a corner.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.M) return;
+  int h[3];
+  R p[3], ar;
+  AxisNodes<R> s[3];
+  if (!marker_setup(a, j, h, p, s, ar)) return;
+  const int n = a.n_sub, nm1 = n - 1;
+  int sc[3];
+  R lam[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const R u = s[d].frac * R(nm1);
+    int q = (int)floor(u);
+    q = q < 0 ? 0 : (q > nm1 - 1 ? nm1 - 1 : q);
+    sc[d] = q;
+    lam[d] = u - R(q);
+  }
+  R d2[8];
+#pragma unroll
+  for (int cidx = 0; cidx < 8; ++cidx) {
+    const R dx = lam[0] - R(cidx & 1), dy = lam[1] - R((cidx >> 1) & 1), dz = lam[2] - R(cidx >> 2);
+    d2[cidx] = dx * dx + dy * dy + dz * dz;
+  }
+  R pre[8], suf[8];
+  pre[0] = R(1);
+#pragma unroll
+  for (int q = 1; q < 8; ++q) pre[q] = pre[q - 1] * d2[q - 1];
+  suf[7] = R(1);
+#pragma unroll
+  for (int q = 6; q >= 0; --q) suf[q] = suf[q + 1] * d2[q + 1];
+  R alpha[8], sum = R(0);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    alpha[q] = pre[q] * suf[q];
+    sum += alpha[q];
+  }
+  const R inv = R(1) / sum;
+  const int cl = a.class_axis >= 0 ? h[a.class_axis] : 0;
+  const R* T = a.table + (int64_t)cl * n * n * n * 27;
+  const R* rows[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    alpha[q] *= inv;
+    rows[q] = T + (int64_t)((((sc[2] + (q >> 2)) * n) + (sc[1] + ((q >> 1) & 1))) * n + (sc[0] + (q & 1))) * 27;
+  }
+  R phi[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    R v = R(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v += alpha[q] * __ldg(&rows[q][k]);
+    phi[k] = v;
+  }
+  marker_store(a, j, h, s, phi, ar);
+}
+
+// Table of exact shape functions at the sub-Eulerian nodes -1/2 + i/(n-1)
+// (faces included) of one home cell per class, computed in double and
+// rounded to R.  A class is the home index along the single non-uniform axis;
+// uniform axes have unit neighbour/home width ratios.
+template <typename R>
+__global__ void k_fast_table(Grid<double> gd, int class_axis, int64_t n_classes, int n_sub, double inv_eps2,
+                             R* __restrict__ table) {
+  const int64_t S3 = (int64_t)n_sub * n_sub * n_sub;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_classes * S3) return;
+  const int64_t cl = idx / S3;
+  const int s = (int)(idx % S3);
+  const int sub[3] = {s % n_sub, (s / n_sub) % n_sub, s / (n_sub * n_sub)};
+  AxisNodes<double> nd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double t = -0.5 + (double)sub[d] / (double)(n_sub - 1);
+    const Axis<double>& ax = gd.ax[d];
+    if (d == class_axis) {
+      const int i = (int)cl;
+      nd[d] = axis_nodes_at(t, width_of(ax, wrap(i - 1, ax.n, ax.periodic)), width_of(ax, i),
+                            width_of(ax, wrap(i + 1, ax.n, ax.periodic)));
+    } else {
+      const double w = width_of(ax, 0);
+      nd[d] = axis_nodes_at(t, w, w, w);
+    }
+  }
+  double phi[27];
+  if (!shape_exact<double>(nd, inv_eps2, 0, phi, nullptr)) {
+    for (int k = 0; k < 27; ++k) phi[k] = 0.0;
+  }
+  for (int k = 0; k < 27; ++k) table[idx * 27 + k] = (R)phi[k];
+}
+
+template <typename R>
+static BuildArgs<R> make_args(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M) {
+  BuildArgs<R> a;
+  a.g = device_grid<R>(ctx);
+  a.gd = device_grid<double>(ctx);
+  a.x = (const R*)x;
+  a.area = (const R*)area;
+  a.perm = T->perm;
+  a.M = M;
+  a.cap = T->cap;
+  a.phi = (R*)T->phi;
+  a.c = (R*)T->c;
+  a.home = T->home;
+  a.status = T->status;
+  a.inv_eps2 = (R)(1.0 / (ctx->opt.eps * ctx->opt.eps));
+  a.inv_eps2_d = 1.0 / (ctx->opt.eps * ctx->opt.eps);
+  a.refine = ctx->opt.real == MLS_F32 ? ctx->opt.refine : 0;
+  a.cond_max = ctx->opt.cond_max;
+  a.table = (const R*)ctx->table;
+  a.class_axis = ctx->class_axis;
+  a.n_sub = ctx->opt.n_sub;
+  return a;
+}
+
+cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                               cudaStream_t s) {
+  const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  if (ctx->opt.real == MLS_F64)
+    k_build_exact<double><<<grid, kBlock, 0, s>>>(make_args<double>(ctx, T, x, area, M));
+  else
+    k_build_exact<float><<<grid, kBlock, 0, s>>>(make_args<float>(ctx, T, x, area, M));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_fast(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                              cudaStream_t s) {
+  const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  if (ctx->opt.real == MLS_F64)
+    k_build_fast<double><<<grid, kBlock, 0, s>>>(make_args<double>(ctx, T, x, area, M));
+  else
+    k_build_fast<float><<<grid, kBlock, 0, s>>>(make_args<float>(ctx, T, x, area, M));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s) {
+  const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
+  const int64_t total = ctx->n_classes * S3;
+  const unsigned grid = (unsigned)((total + 127) / 128);
+  const double inv_eps2 = 1.0 / (ctx->opt.eps * ctx->opt.eps);
+  if (ctx->opt.real == MLS_F64)
+    k_fast_table<double><<<grid, 128, 0, s>>>(device_grid<double>(ctx), ctx->class_axis, ctx->n_classes,
+                                              ctx->opt.n_sub, inv_eps2, (double*)ctx->table);
+  else
+    k_fast_table<float><<<grid, 128, 0, s>>>(device_grid<double>(ctx), ctx->class_axis, ctx->n_classes,
+                                             ctx->opt.n_sub, inv_eps2, (float*)ctx->table);
+  return cudaGetLastError();
+}
+
+}  // namespace mls

@@ -1,0 +1,237 @@
+// Marker preparation (triangle centroids and areas) and the counting sort
+// that groups markers by spreading tile before the build.
+#include "mls_host.h"
+
+namespace mls {
+
+template <typename R> struct Ops;
+template <> struct Ops<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float nan_() { return __int_as_float(0x7fc00000); }
+};
+template <> struct Ops<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double nan_() { return __longlong_as_double(0x7ff8000000000000ULL); }
+};
+
+// Centroid C = ((V1+V2)+V3)/3 and area |(V2-V1)x(V3-V1)|/2 of each triangle,
+// every operation rounded to nearest in R with no contraction, so the result
+// is reproducible bit for bit by any IEEE implementation of the same order.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_prep(const R* __restrict__ V, int64_t nv,
+                                                 const int32_t* __restrict__ tri, int64_t nt,
+                                                 R* __restrict__ x, R* __restrict__ area) {
+  using O = Ops<R>;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int64_t i0 = tri[3 * t], i1 = tri[3 * t + 1], i2 = tri[3 * t + 2];
+  if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+    x[t] = x[nt + t] = x[2 * nt + t] = O::nan_();
+    area[t] = O::nan_();
+    return;
+  }
+  R a[3], b[3], c[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    a[d] = V[3 * i0 + d];
+    b[d] = V[3 * i1 + d];
+    c[d] = V[3 * i2 + d];
+  }
+  R e1[3], e2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    x[d * nt + t] = O::div(O::add(O::add(a[d], b[d]), c[d]), R(3));
+    e1[d] = O::sub(b[d], a[d]);
+    e2[d] = O::sub(c[d], a[d]);
+  }
+  const R nx = O::sub(O::mul(e1[1], e2[2]), O::mul(e1[2], e2[1]));
+  const R ny = O::sub(O::mul(e1[2], e2[0]), O::mul(e1[0], e2[2]));
+  const R nz = O::sub(O::mul(e1[0], e2[1]), O::mul(e1[1], e2[0]));
+  area[t] = O::mul(R(0.5), O::sqrt_(O::add(O::add(O::mul(nx, nx), O::mul(ny, ny)), O::mul(nz, nz))));
+}
+
+cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri, int64_t nt, void* x,
+                        void* area, cudaStream_t s) {
+  if (nt == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((nt + kBlock - 1) / kBlock);
+  if (real == MLS_F64)
+    k_prep<double><<<grid, kBlock, 0, s>>>((const double*)V, nv, tri, nt, (double*)x, (double*)area);
+  else
+    k_prep<float><<<grid, kBlock, 0, s>>>((const float*)V, nv, tri, nt, (float*)x, (float*)area);
+  return cudaGetLastError();
+}
+
+// Home cell of every marker, its spreading-tile bin, and its rank inside the
+// bin (warp-aggregated atomic counter per bin).  Dropped markers go to the
+// last bin and are counted in status[0] (all) and status[1] (non-finite).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R* __restrict__ x,
+                                                   const R* __restrict__ area, int64_t M,
+                                                   int32_t* __restrict__ key, int32_t* __restrict__ rank,
+                                                   int32_t* __restrict__ counts,
+                                                   unsigned long long* __restrict__ status) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const R p[3] = {x[j], x[M + j], x[2 * M + j]};
+  const R ar = area[j];
+  const bool finite = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(ar);
+  bool ok = finite;
+  int h[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    h[d] = locate_axis(g.ax[d], p[d]);
+    ok = ok && support_ok(g.ax[d], h[d]);
+  }
+  int k = tl.nbins - 1;
+  if (ok)
+    k = (((h[2] >> tl.l[2]) * tl.nb[1]) + (h[1] >> tl.l[1])) * tl.nb[0] + (h[0] >> tl.l[0]);
+  const unsigned peers = __match_any_sync(__activemask(), k);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&counts[k], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  key[j] = k;
+  rank[j] = base + __popc(peers & ((1u << lane) - 1u));
+  if (!ok) {
+    atomicAdd(&status[0], 1ULL);
+    if (!finite) atomicAdd(&status[1], 1ULL);
+  }
+}
+
+cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                          cudaStream_t s) {
+  const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  if (ctx->opt.real == MLS_F64)
+    k_locate<double><<<grid, kBlock, 0, s>>>(device_grid<double>(ctx), ctx->tiles, (const double*)x,
+                                             (const double*)area, M, T->key, T->rank, T->counts, T->status);
+  else
+    k_locate<float><<<grid, kBlock, 0, s>>>(device_grid<float>(ctx), ctx->tiles, (const float*)x,
+                                            (const float*)area, M, T->key, T->rank, T->counts, T->status);
+  return cudaGetLastError();
+}
+
+// ---- exclusive scan of the bin counts (three passes, no inter-block waits) ----
+
+constexpr int kScanThreads = 512;
+constexpr int kScanPer = kScanTile / kScanThreads;  // 8 bins per thread
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    int w = lane < nw ? warp_tot[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int n = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += n;
+    }
+    if (lane < nw) warp_tot[lane] = wi - w;
+    if (lane == nw - 1) *total = wi;
+  }
+  __syncthreads();
+  return incl - v + warp_tot[wid];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __restrict__ counts, int nbins,
+                                                              int32_t* __restrict__ tile_sums) {
+  __shared__ int warp_tot[32];
+  __shared__ int total;
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  int v = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q)
+    if (base + q < nbins) v += counts[base + q];
+  block_exclusive_scan(v, warp_tot, &total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(int32_t* __restrict__ tile_sums, int ntiles) {
+  __shared__ int warp_tot[32];
+  __shared__ int total;
+  constexpr int per = kScanMaxTiles / 1024;
+  int v[per];
+  int s = 0;
+#pragma unroll
+  for (int q = 0; q < per; ++q) {
+    const int i = threadIdx.x * per + q;
+    v[q] = i < ntiles ? tile_sums[i] : 0;
+    s += v[q];
+  }
+  int run = block_exclusive_scan(s, warp_tot, &total);
+#pragma unroll
+  for (int q = 0; q < per; ++q) {
+    const int i = threadIdx.x * per + q;
+    if (i < ntiles) tile_sums[i] = run;
+    run += v[q];
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* __restrict__ counts, int nbins,
+                                                             const int32_t* __restrict__ tile_sums,
+                                                             int32_t* __restrict__ offsets) {
+  __shared__ int warp_tot[32];
+  __shared__ int total;
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = base + q < nbins ? counts[base + q] : 0;
+    s += v[q];
+  }
+  int run = block_exclusive_scan(s, warp_tot, &total) + tile_sums[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    if (base + q < nbins) offsets[base + q] = run;
+    run += v[q];
+  }
+}
+
+cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx) {
+  const int ntiles = (nbins + kScanTile - 1) / kScanTile;
+  int slot = timer_begin(ctx, "scan_reduce", s);
+  k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, T->tile_sums);
+  timer_end(ctx, slot, s);
+  slot = timer_begin(ctx, "scan_tiles", s);
+  k_scan_tiles<<<1, 1024, 0, s>>>(T->tile_sums, ntiles);
+  timer_end(ctx, slot, s);
+  slot = timer_begin(ctx, "scan_apply", s);
+  k_scan_apply<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, T->tile_sums, T->offsets);
+  timer_end(ctx, slot, s);
+  return cudaGetLastError();
+}
+
+// perm[offsets[bin] + rank] = caller index: stable within nothing, grouped by bin.
+__global__ void __launch_bounds__(kBlock) k_scatter(const int32_t* __restrict__ key, const int32_t* __restrict__ rank,
+                                                    const int32_t* __restrict__ offsets, int64_t M,
+                                                    int32_t* __restrict__ perm) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  perm[offsets[key[j]] + rank[j]] = (int32_t)j;
+}
+
+cudaError_t launch_scatter(mls_transfer* T, int64_t M, cudaStream_t s) {
+  const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  k_scatter<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->perm);
+  return cudaGetLastError();
+}
+
+}  // namespace mls

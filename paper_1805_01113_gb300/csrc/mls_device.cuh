@@ -1,0 +1,299 @@
+// Device-side building blocks of the MLS transfer library: grid description,
+// home-cell location, per-axis support geometry and the two shape-function
+// evaluations (exact-MLS, Eqs. 3-6; fast-MLS, Eqs. 9-10).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace mls {
+
+// One grid axis.  Cell i spans [faces[i], faces[i+1]); `uniform` axes also
+// carry lo and h so the home cell comes from one multiply plus a face check.
+template <typename R>
+struct Axis {
+  const R* faces;   // n+1 values (device)
+  const R* widths;  // n values (device)
+  R lo, hi, h;      // faces[0], faces[n], width when uniform
+  int n;
+  int periodic;
+  int uniform;
+};
+
+template <typename R>
+struct Grid {
+  Axis<R> ax[3];
+};
+
+// Spreading tiles: 2^l home cells per axis; bins = tiles + 1 (the last bin
+// collects dropped markers).
+struct Tiles {
+  int l[3];
+  int nb[3];
+  int nbins;
+};
+
+// Home cell of coordinate x on one axis: face_i <= x < face_{i+1}.  Returns -1
+// outside [faces[0], faces[n]) or for NaN.  Uniform axes guess i from
+// (x - lo)/h and correct it against the face array, so the result agrees with
+// the exact comparison whatever the rounding of the guess.
+template <typename R>
+__device__ __forceinline__ int locate_axis(const Axis<R>& a, R x) {
+  if (!(x >= a.lo && x < a.hi)) return -1;
+  int i;
+  if (a.uniform) {
+    R s = (x - a.lo) / a.h;
+    i = (int)s;
+    i = i < 0 ? 0 : (i > a.n - 1 ? a.n - 1 : i);
+    if (x < a.faces[i]) --i;
+    else if (x >= a.faces[i + 1]) ++i;
+  } else {
+    int lo = 0, hi = a.n;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (a.faces[mid] <= x) lo = mid; else hi = mid;
+    }
+    i = lo;
+  }
+  return i;
+}
+
+// A home index is usable when the 3-wide support stays on the grid (always on
+// periodic axes, which wrap).
+template <typename R>
+__device__ __forceinline__ bool support_ok(const Axis<R>& a, int i) {
+  return i >= 0 && (a.periodic || (i >= 1 && i <= a.n - 2));
+}
+
+__device__ __forceinline__ int wrap(int j, int n, int periodic) {
+  if (periodic) return j < 0 ? j + n : (j >= n ? j - n : j);
+  return j < 0 ? 0 : (j >= n ? n - 1 : j);
+}
+
+template <typename R>
+__device__ __forceinline__ R width_of(const Axis<R>& a, int j) {
+  return a.uniform ? a.h : a.widths[j];
+}
+
+// Geometry of the 3 support nodes of one axis, in units of the home cell's
+// width: xi[a] = (x_node - x_l)/Delta_home, node widths w[a] (physical), the
+// marker's position frac in [0, 1) across the home cell and t = frac - 1/2,
+// its offset from the home-cell centre.
+template <typename R>
+struct AxisNodes {
+  R xi[3];
+  R w[3];
+  R frac;
+  R t;
+};
+
+template <typename R>
+__device__ __forceinline__ AxisNodes<R> axis_nodes(const Axis<R>& a, int i, R x) {
+  AxisNodes<R> s;
+  const R wh = width_of(a, i);
+  const R wm = width_of(a, wrap(i - 1, a.n, a.periodic));
+  const R wp = width_of(a, wrap(i + 1, a.n, a.periodic));
+  s.frac = (x - a.faces[i]) / wh;
+  s.t = s.frac - R(0.5);
+  s.xi[0] = -(R(0.5) + R(0.5) * (wm / wh)) - s.t;
+  s.xi[1] = -s.t;
+  s.xi[2] = (R(0.5) + R(0.5) * (wp / wh)) - s.t;
+  s.w[0] = wm;
+  s.w[1] = wh;
+  s.w[2] = wp;
+  return s;
+}
+
+// Node geometry at a prescribed offset t with neighbour/home width ratios
+// rm, rp (used to tabulate fast-MLS shape functions on the sub-Eulerian mesh).
+template <typename R>
+__device__ __forceinline__ AxisNodes<R> axis_nodes_at(R t, R wm, R wh, R wp) {
+  AxisNodes<R> s;
+  s.t = t;
+  s.frac = t + R(0.5);
+  s.xi[0] = -(R(0.5) + R(0.5) * (wm / wh)) - t;
+  s.xi[1] = -t;
+  s.xi[2] = (R(0.5) + R(0.5) * (wp / wh)) - t;
+  s.w[0] = wm;
+  s.w[1] = wh;
+  s.w[2] = wp;
+  return s;
+}
+
+template <typename R> __device__ __forceinline__ R dev_exp(R v);
+template <> __device__ __forceinline__ float dev_exp<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ double dev_exp<double>(double v) { return exp(v); }
+
+// 4x4 symmetric positive definite solve by Cholesky, A packed lower-triangular
+// row by row: a00 a10 a11 a20 a21 a22 a30 a31 a32 a33.
+template <typename R>
+struct Chol4 {
+  R l10, l20, l21, l30, l31, l32;
+  R i0, i1, i2, i3;   // reciprocals of the diagonal of L
+  bool ok;
+
+  __device__ __forceinline__ void factor(const R a[10]) {
+    R d0 = a[0];
+    ok = d0 > R(0);
+    R l00 = sqrt(d0);
+    i0 = R(1) / l00;
+    l10 = a[1] * i0;
+    l20 = a[3] * i0;
+    l30 = a[6] * i0;
+    R d1 = a[2] - l10 * l10;
+    ok = ok && d1 > R(0);
+    i1 = R(1) / sqrt(d1);
+    l21 = (a[4] - l20 * l10) * i1;
+    l31 = (a[7] - l30 * l10) * i1;
+    R d2 = a[5] - l20 * l20 - l21 * l21;
+    ok = ok && d2 > R(0);
+    i2 = R(1) / sqrt(d2);
+    l32 = (a[8] - l30 * l20 - l31 * l21) * i2;
+    R d3 = a[9] - l30 * l30 - l31 * l31 - l32 * l32;
+    ok = ok && d3 > R(0);
+    i3 = R(1) / sqrt(d3);
+  }
+
+  __device__ __forceinline__ void solve(const R b[4], R y[4]) const {
+    R z0 = b[0] * i0;
+    R z1 = (b[1] - l10 * z0) * i1;
+    R z2 = (b[2] - l20 * z0 - l21 * z1) * i2;
+    R z3 = (b[3] - l30 * z0 - l31 * z1 - l32 * z2) * i3;
+    y[3] = z3 * i3;
+    y[2] = (z2 - l32 * y[3]) * i2;
+    y[1] = (z1 - l21 * y[2] - l31 * y[3]) * i1;
+    y[0] = (z0 - l10 * y[1] - l20 * y[2] - l30 * y[3]) * i0;
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ void sym_mul(const R a[10], const R y[4], R out[4]) {
+  out[0] = a[0] * y[0] + a[1] * y[1] + a[3] * y[2] + a[6] * y[3];
+  out[1] = a[1] * y[0] + a[2] * y[1] + a[4] * y[2] + a[7] * y[3];
+  out[2] = a[3] * y[0] + a[4] * y[1] + a[5] * y[2] + a[8] * y[3];
+  out[3] = a[6] * y[0] + a[7] * y[1] + a[8] * y[2] + a[9] * y[3];
+}
+
+// 1-norm condition number of the packed SPD matrix from its Cholesky factor.
+template <typename R>
+__device__ __forceinline__ R cond1(const R a[10], const Chol4<R>& ch) {
+  R colsum[4] = {
+      fabs(a[0]) + fabs(a[1]) + fabs(a[3]) + fabs(a[6]),
+      fabs(a[1]) + fabs(a[2]) + fabs(a[4]) + fabs(a[7]),
+      fabs(a[3]) + fabs(a[4]) + fabs(a[5]) + fabs(a[8]),
+      fabs(a[6]) + fabs(a[7]) + fabs(a[8]) + fabs(a[9])};
+  R an = fmax(fmax(colsum[0], colsum[1]), fmax(colsum[2], colsum[3]));
+  R inv_n = R(0);
+  for (int c = 0; c < 4; ++c) {
+    R e[4] = {R(0), R(0), R(0), R(0)};
+    e[c] = R(1);
+    R y[4];
+    ch.solve(e, y);
+    inv_n = fmax(inv_n, fabs(y[0]) + fabs(y[1]) + fabs(y[2]) + fabs(y[3]));
+  }
+  return an * inv_n;
+}
+
+// Exact-MLS shape functions of one marker from its per-axis node geometry.
+//   Eq. 3: A = sum_k W_k p_k p_k^T with p_k = [1, xi_x, xi_y, xi_z] (marker-
+//          centred, home-width-scaled basis, an affine change of [1,x,y,z]
+//          under which Phi is invariant), W_k = exp(-|xi_k|^2/eps^2)
+//          evaluated as the product of three per-axis factors.
+//   Eq. 6: Phi^T = p^T(x_l) A^-1 B = e_0^T A^-1 B, i.e. phi_k = W_k (y . p_k)
+//          with A y = e_0 (A is symmetric).
+// `refine` extra residual-correction steps are applied to y.  Returns false
+// if A is not numerically positive definite; `cond` (if non-null) receives
+// cond_1(A).
+template <typename R>
+__device__ __forceinline__ bool shape_exact(const AxisNodes<R> s[3], R inv_eps2, int refine, R phi[27],
+                                            R* cond) {
+  R w[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w[d][a] = dev_exp<R>(-(s[d].xi[a] * s[d].xi[a]) * inv_eps2);
+
+  R A[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) A[q] = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R W = w[0][a] * w[1][b] * w[2][c];
+        const R px = s[0].xi[a], py = s[1].xi[b], pz = s[2].xi[c];
+        const R Wx = W * px, Wy = W * py, Wz = W * pz;
+        A[0] += W;
+        A[1] += Wx;
+        A[2] += Wx * px;
+        A[3] += Wy;
+        A[4] += Wy * px;
+        A[5] += Wy * py;
+        A[6] += Wz;
+        A[7] += Wz * px;
+        A[8] += Wz * py;
+        A[9] += Wz * pz;
+      }
+
+  Chol4<R> ch;
+  ch.factor(A);
+  if (!ch.ok) return false;
+  const R e0[4] = {R(1), R(0), R(0), R(0)};
+  R y[4];
+  ch.solve(e0, y);
+  for (int it = 0; it < refine; ++it) {
+    R Ay[4], r[4], dy[4];
+    sym_mul(A, y, Ay);
+    r[0] = R(1) - Ay[0];
+    r[1] = -Ay[1];
+    r[2] = -Ay[2];
+    r[3] = -Ay[3];
+    ch.solve(r, dy);
+    y[0] += dy[0];
+    y[1] += dy[1];
+    y[2] += dy[2];
+    y[3] += dy[3];
+  }
+  if (cond) *cond = cond1(A, ch);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R W = w[0][a] * w[1][b] * w[2][c];
+        phi[9 * c + 3 * b + a] = W * (y[0] + y[1] * s[0].xi[a] + y[2] * s[1].xi[b] + y[3] * s[2].xi[c]);
+      }
+  return true;
+}
+
+// c_l of Eq. 8 with h_l = sum_k phi_k (Dx_k + Dy_k + Dz_k)/3 and
+// Delta V_l = A_l h_l; node widths are separable, so both sums run over
+// per-axis marginals of phi.
+template <typename R>
+__device__ __forceinline__ R scale_factor(const AxisNodes<R> s[3], const R phi[27], R area) {
+  R mx[3] = {R(0), R(0), R(0)}, my[3] = {R(0), R(0), R(0)}, mz[3] = {R(0), R(0), R(0)};
+  R vol = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R p = phi[9 * c + 3 * b + a];
+        mx[a] += p;
+        my[b] += p;
+        mz[c] += p;
+        vol += p * (s[0].w[a] * s[1].w[b] * s[2].w[c]);
+      }
+  R hsum = R(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) hsum += mx[a] * s[0].w[a] + my[a] * s[1].w[a] + mz[a] * s[2].w[a];
+  const R h_l = hsum / R(3);
+  return (area * h_l) / vol;
+}
+
+}  // namespace mls

@@ -1,0 +1,99 @@
+// Host-side state of the MLS transfer library and the kernel launchers the
+// C ABI (mls_api.cu) calls.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mls.h"
+#include "mls_device.cuh"
+
+struct mls_kernel_timer {
+  const char* name;
+  int64_t launches;
+  double total_ms;
+};
+
+struct mls_event_pair {
+  int timer;
+  cudaEvent_t start, stop;
+};
+
+struct mls_ctx {
+  mls_options opt;
+  int device;
+  int n[3];
+  int periodic[3];
+  int uniform[3];
+  // Grid on the device in both precisions (faces n+1, widths n per axis).
+  double* faces_d[3];
+  double* widths_d[3];
+  float* faces_f[3];
+  float* widths_f[3];
+  std::vector<double> faces_host[3];
+  mls::Tiles tiles;
+  // Fast-MLS table, real[n_classes][n_sub^3][27]; class axis -1 when uniform.
+  void* table;
+  int64_t n_classes;
+  int class_axis;
+  // Per-kernel timing.
+  int timing;
+  std::vector<mls_kernel_timer> timers;
+  std::vector<mls_event_pair> events;
+  size_t events_used;
+};
+
+struct mls_transfer {
+  mls_ctx* ctx;
+  int64_t cap;
+  int64_t M;
+  int method;
+  void* phi;         // real[27][cap]
+  void* c;           // real[cap]
+  int32_t* home;     // [cap] tile order
+  int32_t* perm;     // [cap] tile order -> caller index
+  int32_t* key;      // [cap] caller order: tile bin
+  int32_t* rank;     // [cap] caller order: rank inside the bin
+  int32_t* counts;   // [nbins]
+  int32_t* offsets;  // [nbins]
+  int32_t* tile_sums;
+  int ntiles;        // scan tiles over the bins
+  unsigned long long* status;  // [4] dropped, nonfinite, refined_fp64, spare
+};
+
+namespace mls {
+
+constexpr int kScanTile = 4096;       // bins per scan tile
+constexpr int kScanMaxTiles = 8192;   // bins <= 32 Mi
+constexpr int kBlock = 256;           // threads per block of the per-marker kernels
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Timing helpers (no-ops unless ctx->timing).
+int timer_begin(mls_ctx* ctx, const char* name, cudaStream_t s);
+void timer_end(mls_ctx* ctx, int slot, cudaStream_t s);
+
+template <typename R> Grid<R> device_grid(const mls_ctx* ctx);
+
+// Launchers; each returns cudaGetLastError() after enqueueing.
+cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri, int64_t nt, void* x,
+                        void* area, cudaStream_t s);
+cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                          cudaStream_t s);
+cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx);
+cudaError_t launch_scatter(mls_transfer* T, int64_t M, cudaStream_t s);
+cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                               cudaStream_t s);
+cudaError_t launch_build_fast(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                              cudaStream_t s);
+cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s);
+cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s);
+cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s);
+size_t spread_smem_bytes(const mls_ctx* ctx);
+cudaError_t spread_configure(const mls_ctx* ctx);
+
+}  // namespace mls

@@ -1,0 +1,335 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances (normwise, max|gpu - oracle| / max|oracle| per output array):
+double 1e-12, single 1e-5, bfloat16-stored spread field 1e-2.  Sizes span
+many spreading tiles and blocks with ragged tails; the full-size multi-body
+case runs in the launch configuration the benchmark times and is checked on
+sampled markers and cells plus conservation and adjointness.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import DEV, NP_DT, fast_tie_fix, home_linear, normwise, run_gpu, run_oracle
+from workloads import make_workload, tanh_faces, uniform_faces
+from workloads.fields import field_full_np, field_full_torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1805_01113_gb300 import api as _api
+    torch.cuda.set_device(0)
+    return _api
+
+
+def _compare(g, r, tol, keys=("phi", "c", "U", "f")):
+    errs = {k: normwise(g[k], r[k]) for k in keys if k in g and k in r}
+    assert all(e <= tol for e in errs.values()), errs
+    return errs
+
+
+@pytest.mark.parametrize("real", ["f64", "f32"])
+def test_marker_prep_bit_exact(api, real):
+    w = make_workload("c2", n=128, n_bodies=40)
+    ctx = api.Context(w.faces, w.periodic, real=real)
+    V = w.vertices.astype(NP_DT[real])
+    tri = w.tri.copy()
+    tri[5] = [0, 1, len(V)]                                # out-of-range vertex index
+    x, a = ctx.marker_prep(torch.as_tensor(V, device=DEV), torch.as_tensor(tri, device=DEV))
+    xr, ar = oracle.marker_prep(V, np.where(tri < len(V), tri, 0), real)
+    xg, ag = x.cpu().numpy(), a.cpu().numpy()
+    good = np.ones(len(tri), bool)
+    good[5] = False
+    assert np.isnan(xg[:, 5]).all() and np.isnan(ag[5])
+    assert np.array_equal(xg[:, good], xr[:, good])
+    assert np.array_equal(ag[good], ar[good])
+
+
+@pytest.mark.parametrize("method", ["exact", "fast"])
+def test_single_sphere_f64(api, method):
+    """One level-4 icosphere (5120 markers) in a periodic 64^3 grid, double precision."""
+    w = make_workload("c1")
+    grid = oracle.Grid(w.faces, w.periodic)
+    x, area = oracle.marker_prep(w.vertices, w.tri, "f64")
+    u = field_full_np(w.modes, w.faces)
+    F = w.forces()
+    ctx = api.Context(w.faces, w.periodic, real="f64")
+    g = run_gpu(ctx, x, area, method, torch.as_tensor(u, device=DEV), F)
+    r = run_oracle(grid, x, area, method, u, F)
+    assert g["status"]["dropped"] == 0
+    assert np.array_equal(g["home"], home_linear(r["tr"].sup, grid.n))
+    _compare(g, r, TOL["f64"])
+    assert np.all(g["f"][r["f"] == 0] == 0)               # untouched cells stay exactly zero
+
+
+@pytest.mark.parametrize("method", ["exact", "fast"])
+def test_multibody_f32(api, method):
+    """48 ellipsoids (61440 markers) in a periodic 128^3 grid, single precision."""
+    w = make_workload("c2", n=128, n_bodies=48)
+    grid = oracle.Grid(w.faces, w.periodic)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    u = field_full_np(w.modes, w.faces, np.float32)
+    F = w.forces().astype(np.float32)
+    ctx = api.Context(w.faces, w.periodic, real="f32")
+    g = run_gpu(ctx, x, area, method, torch.as_tensor(u, device=DEV), F)
+    r = run_oracle(grid, x, area, method, u, F)
+    assert g["status"]["dropped"] == 0
+    assert np.array_equal(g["home"], home_linear(r["tr"].sup, grid.n))
+    if method == "fast":
+        _, unresolved = fast_tie_fix(grid, x, g["phi"], r["phi"], TOL["f32"])
+        assert unresolved == 0
+        _compare(g, r, TOL["f32"], ("c", "U", "f"))
+    else:
+        _compare(g, r, TOL["f32"])
+
+
+@pytest.mark.parametrize("method", ["exact", "fast"])
+def test_stretched_f32(api, method):
+    """Deformed bodies in a grid tanh-stretched and walled in z (one table per z cell for fast-MLS)."""
+    w = make_workload("c3", n=96, n_bodies=16)
+    grid = oracle.Grid(w.faces, w.periodic)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    u = field_full_np(w.modes, w.faces, np.float32)
+    F = w.forces().astype(np.float32)
+    ctx = api.Context(w.faces, w.periodic, real="f32")
+    g = run_gpu(ctx, x, area, method, torch.as_tensor(u, device=DEV), F)
+    r = run_oracle(grid, x, area, method, u, F)
+    assert g["status"]["dropped"] == 0
+    assert np.array_equal(g["home"], home_linear(r["tr"].sup, grid.n))
+    if method == "fast":
+        resolved, unresolved = fast_tie_fix(grid, x, g["phi"], r["phi"], TOL["f32"])
+        assert unresolved == 0 and resolved <= max(3, 1e-4 * x.shape[1])
+        if resolved == 0:
+            _compare(g, r, TOL["f32"], ("c", "U", "f"))
+    else:
+        _compare(g, r, TOL["f32"])
+
+
+def _below(v, real):
+    """Largest number of the path's precision below v."""
+    dt = NP_DT[real]
+    return float(np.nextafter(dt(v), dt(-np.inf)))
+
+
+def _edge_markers(n, rng, real):
+    """1000 random markers plus faces, periodic seams, walls, NaN/inf and outside points."""
+    faces = [uniform_faces(n), uniform_faces(n), tanh_faces(n, 1.5)]
+    x = np.empty((3, 1000))
+    for d in range(3):
+        x[d] = rng.uniform(faces[d][1], faces[d][n - 1], size=1000)
+    special = [
+        (faces[0][3], faces[1][5], faces[2][4]),            # exactly on faces: lower cell wins
+        (faces[0][0], faces[1][0], faces[2][2]),            # periodic seam at the low end
+        (_below(faces[0][n], real), _below(faces[1][n], real), faces[2][n - 2]),  # just below the high end
+        (0.1, 0.2, 0.5 * (faces[2][0] + faces[2][1])),     # wall cell z=0: dropped
+        (0.1, 0.2, 0.5 * (faces[2][n - 1] + faces[2][n])),  # wall cell z=n-1: dropped
+        (np.nan, 0.0, 0.0),                                 # non-finite: dropped
+        (1.0, 0.0, 0.0),                                    # x = upper face: outside, dropped
+        (-1.5, 0.0, 0.0),                                   # outside: dropped
+        (0.0, 0.0, 0.0),                                    # area = inf below: dropped
+    ]
+    x = np.concatenate([x, np.array(special, dtype=np.float64).T], axis=1).astype(NP_DT[real])
+    area = rng.uniform(0.5, 1.5, size=x.shape[1]).astype(NP_DT[real]) * (2.0 / n) ** 2
+    area[-1] = np.inf
+    return faces, (True, True, False), x, area, 6, 2
+
+
+@pytest.mark.parametrize("real", ["f64", "f32"])
+@pytest.mark.parametrize("method", ["exact", "fast"])
+def test_edge_markers(api, real, method):
+    rng = np.random.default_rng(17)
+    n = 16
+    faces, periodic, x, area, n_drop, n_nonfinite = _edge_markers(n, rng, real)
+    grid = oracle.Grid(faces, periodic)
+    M = x.shape[1]
+    u = rng.normal(size=(3, n, n, n)).astype(NP_DT[real])
+    F = rng.normal(size=(3, M)).astype(NP_DT[real])
+    ctx = api.Context(faces, periodic, real=real)
+    g = run_gpu(ctx, x, area, method, torch.as_tensor(u, device=DEV), F)
+    r = run_oracle(grid, x, area, method, u, F)
+    st = g["status"]
+    assert st["dropped"] == n_drop and st["nonfinite"] == n_nonfinite
+    dropped = ~r["tr"].sup.ok
+    assert dropped.sum() == n_drop
+    assert np.array_equal(g["home"], home_linear(r["tr"].sup, grid.n))
+    assert np.all(g["phi"][dropped] == 0) and np.all(g["c"][dropped] == 0) and np.all(g["U"][:, dropped] == 0)
+    keys = ("phi", "c", "U", "f")
+    if method == "fast" and real == "f32":
+        resolved, unresolved = fast_tie_fix(grid, x, g["phi"], r["phi"], TOL[real])
+        assert unresolved == 0
+        keys = ("c", "U", "f") if resolved == 0 else ("c",)
+    _compare(g, r, TOL[real], keys)
+
+
+def test_empty_and_capacity(api):
+    faces = [uniform_faces(8)] * 3
+    ctx = api.Context(faces, (True, True, True), real="f32")
+    T = ctx.transfer(10)
+    x = torch.empty((3, 0), dtype=torch.float32, device=DEV)
+    a = torch.empty((0,), dtype=torch.float32, device=DEV)
+    ctx.build_transfer(T, x, a)
+    u = torch.ones((3, 8, 8, 8), dtype=torch.float32, device=DEV)
+    assert ctx.interpolate(T, u).shape == (3, 0)
+    f = torch.zeros_like(u)
+    ctx.spread(T, torch.empty((3, 0), dtype=torch.float32, device=DEV), f)
+    assert ctx.status(T)["dropped"] == 0 and float(f.abs().sum()) == 0.0
+    from paper_1805_01113_gb300 import binding as B
+    x11 = torch.zeros((3, 11), dtype=torch.float32, device=DEV)
+    with pytest.raises(B.MlsError) as e:
+        ctx.build_transfer(T, x11, torch.ones(11, dtype=torch.float32, device=DEV))
+    assert e.value.code == B.MLS_ERR_CAPACITY
+
+
+def test_crowded_tile(api):
+    """3000 markers inside two cells: one tile split over many blocks and runs."""
+    rng = np.random.default_rng(5)
+    n = 24
+    faces = [uniform_faces(n)] * 3
+    grid = oracle.Grid(faces, (True, True, True))
+    h = 2.0 / n
+    x = (-1.0 + h * np.array([[9.0], [9.0], [9.0]]) + rng.uniform(0, [[2 * h], [h], [h]], size=(3, 3000)))
+    x = x.astype(np.float32)
+    area = np.full(3000, 0.01 * h * h, dtype=np.float32)
+    u = rng.normal(size=(3, n, n, n)).astype(np.float32)
+    F = rng.normal(size=(3, 3000)).astype(np.float32)
+    ctx = api.Context(faces, (True, True, True), real="f32")
+    g = run_gpu(ctx, x, area, "exact", torch.as_tensor(u, device=DEV), F)
+    r = run_oracle(grid, x, area, "exact", u, F)
+    _compare(g, r, TOL["f32"])
+
+
+@pytest.mark.parametrize("brick", [(1, 1, 1), (2, 3, 4), (5, 5, 1)])
+def test_tile_shapes(api, brick):
+    w = make_workload("c2", n=64, n_bodies=12)
+    grid = oracle.Grid(w.faces, w.periodic)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    u = field_full_np(w.modes, w.faces, np.float32)
+    F = w.forces().astype(np.float32)
+    ctx = api.Context(w.faces, w.periodic, real="f32", brick_log2=brick)
+    g = run_gpu(ctx, x, area, "exact", torch.as_tensor(u, device=DEV), F)
+    r = run_oracle(grid, x, area, "exact", u, F)
+    _compare(g, r, TOL["f32"])
+
+
+def test_double_fallback_on_conditioning(api):
+    """cond_max = 1 forces every single-precision solve through the double path."""
+    w = make_workload("c2", n=64, n_bodies=6)
+    grid = oracle.Grid(w.faces, w.periodic)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    ctx = api.Context(w.faces, w.periodic, real="f32", cond_max=1.0)
+    g = run_gpu(ctx, x, area, "exact")
+    r = run_oracle(grid, x, area, "exact")
+    assert g["status"]["refined_fp64"] == x.shape[1]
+    assert normwise(g["phi"], r["phi"]) <= 1e-6
+    ctx2 = api.Context(w.faces, w.periodic, real="f32")
+    assert run_gpu(ctx2, x, area, "exact")["status"]["refined_fp64"] == 0
+
+
+def test_bf16_fields(api):
+    """bfloat16 field storage with float accumulation: interpolation from identical inputs
+    stays at single-precision accuracy; the spread field is rounded to bfloat16."""
+    w = make_workload("c2", n=64, n_bodies=12)
+    grid = oracle.Grid(w.faces, w.periodic)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    u = torch.as_tensor(field_full_np(w.modes, w.faces), device=DEV).to(torch.bfloat16)
+    F = w.forces().astype(np.float32)
+    ctx = api.Context(w.faces, w.periodic, real="f32", field="bf16")
+    g = run_gpu(ctx, x, area, "exact", u, F)
+    r = run_oracle(grid, x, area, "exact", u.double().cpu().numpy(), F)
+    assert normwise(g["U"], r["U"]) <= TOL["f32"]
+    assert normwise(g["f"], r["f"]) <= 1e-2
+
+
+def test_rebuild_is_deterministic_per_marker(api):
+    w = make_workload("c2", n=64, n_bodies=10)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    u = torch.as_tensor(field_full_np(w.modes, w.faces, np.float32), device=DEV)
+    ctx = api.Context(w.faces, w.periodic, real="f32")
+    T = ctx.transfer(x.shape[1])
+    a = run_gpu(ctx, x, area, "exact", u, T=T)
+    b = run_gpu(ctx, x, area, "exact", u, T=T)
+    assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["U"], b["U"])
+
+
+def _neighbour_markers(home3, n, cell):
+    """Indices of markers whose home cell lies within +/-1 (periodic) of `cell`."""
+    d = [(home3[a] - cell[a] + 1) % n[a] for a in range(3)]
+    return np.nonzero((d[0] <= 2) & (d[1] <= 2) & (d[2] <= 2))[0]
+
+
+def test_full_size_multibody_sampled(api):
+    """2000 ellipsoids (2.56 M markers) in 512^3, the benchmark's workload and launch shape."""
+    w = make_workload("c2")
+    grid = oracle.Grid(w.faces, w.periodic)
+    n = grid.n
+    M = w.n_markers
+    ctx = api.Context(w.faces, w.periodic, real="f32")
+    V32 = w.vertices.astype(np.float32)
+    x, area = ctx.marker_prep(torch.as_tensor(V32, device=DEV), torch.as_tensor(w.tri, device=DEV))
+    u = field_full_torch(w.modes, w.faces, torch.float32, DEV)
+    F = torch.as_tensor(w.forces().astype(np.float32), device=DEV)
+    T = ctx.transfer(M)
+    ctx.build_transfer(T, x, area, "exact")
+    U = ctx.interpolate(T, u)
+    f = torch.zeros_like(u)
+    ctx.spread(T, F, f)
+    assert ctx.status(T)["dropped"] == 0
+    phi_g, c_g, _ = __import__("gpu_helpers").gpu_transfer(ctx, T)
+
+    rng = np.random.default_rng(99)
+    s = rng.choice(M, size=2000, replace=False)
+    xs, as_ = oracle.marker_prep(V32, w.tri[s], "f32")
+    assert np.array_equal(x[:, s].cpu().numpy(), xs)
+    tr = oracle.shape_exact(grid, xs, 1.0)
+    cs = oracle.forcing_scale(tr, as_)
+    assert normwise(phi_g[s], tr.phi) <= TOL["f32"]
+    assert normwise(c_g[s], cs) <= TOL["f32"]
+    ix, iy, iz = (torch.as_tensor(a, device=DEV) for a in tr.sup.idx)
+    usup = u[:, iz, iy, ix].double().cpu().numpy()               # input bytes at the supports
+    U_ref = np.einsum("mk,cmk->cm", tr.phi, usup)
+    assert normwise(U[:, s].double().cpu().numpy(), U_ref) <= TOL["f32"]
+
+    # Spread, element by element on sampled touched cells: every marker whose
+    # support covers the cell, recomputed by the oracle.
+    xall = x.double().cpu().numpy()
+    home3, ok = oracle.locate(grid, xall)
+    assert ok.all()
+    Fh = F.double().cpu().numpy()
+    areah = area.double().cpu().numpy()
+    fh_nonzero = torch.nonzero(f[0].reshape(-1) != 0).squeeze(1).cpu().numpy()
+    cells = rng.choice(fh_nonzero, size=150, replace=False)
+    ref, got = [], []
+    fflat = f.reshape(3, -1)
+    for key in cells:
+        cell = (key % n[0], (key // n[0]) % n[1], key // (n[0] * n[1]))
+        ml = _neighbour_markers(home3, n, cell)
+        trm = oracle.shape_exact(grid, xall[:, ml], 1.0)
+        cm = oracle.forcing_scale(trm, areah[ml])
+        lin = (trm.sup.idx[2] * n[1] + trm.sup.idx[1]) * n[0] + trm.sup.idx[0]
+        w_ = np.where(lin == key, trm.phi, 0.0).sum(1) * cm
+        ref.append((w_[None, :] * Fh[:, ml]).sum(1))
+        got.append(fflat[:, key].double().cpu().numpy())
+    assert normwise(np.array(got), np.array(ref)) <= TOL["f32"]
+
+    # Conservation (Eq. 7) on a uniform grid: sum_k f_k h^3 = sum_l F_l A_l h.
+    h = 2.0 / n[0]
+    lhs = f.double().sum(dim=(1, 2, 3)).cpu().numpy() * h ** 3
+    rhs = (Fh * areah).sum(1) * h
+    scale = (np.abs(Fh) * areah).sum(1) * h
+    assert np.all(np.abs(lhs - rhs) <= 1e-5 * scale)
+    # Adjointness: <U, c F> = <u, f>.
+    v = ctx.view(T)
+    cF = torch.zeros_like(F, dtype=torch.float64)
+    cF[:, v["perm"].long()] = v["c"].double()[None, :] * F.double()[:, v["perm"].long()]
+    a1 = float((U.double() * cF).sum())
+    a2 = float((u.double() * f.double()).sum())
+    a_scale = float((U.double().abs() * cF.abs()).sum())
+    assert abs(a1 - a2) <= 1e-5 * a_scale
