@@ -266,7 +266,7 @@ def shape_fast(grid, x, eps=1.0, n_sub=9, home=None, subcell=None, tables=None):
     t = np.empty((3, M))
     for d in range(3):
         t[d] = (x[d] - grid.faces[d][sup.home[d]]) / sup.hwidth[d] - 0.5
-    u = (t + 0.5) * nm1
+    u = np.where(sup.ok, (t + 0.5) * nm1, 0.0)
     if subcell is None:
         s = np.minimum(np.floor(u), nm1 - 1).astype(np.int64)
     else:
