@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sample-bodies", type=int, default=160, help="bodies in the CPU oracle sample")
+    p.add_argument("--grid", type=int, default=None, help="cells per axis (smaller profiling cases)")
+    p.add_argument("--bodies", type=int, default=None, help="number of bodies (smaller profiling cases)")
     return p.parse_args()
 
 
@@ -69,9 +71,14 @@ def dist_env():
     return rank, world, local
 
 
-def workload(name):
+def workload(name, grid=None, bodies=None):
     from workloads import make_workload
-    return make_workload(name)
+    kw = {}
+    if grid is not None:
+        kw["n"] = grid
+    if bodies is not None and name != "c1":
+        kw["n_bodies"] = bodies
+    return make_workload(name, **kw)
 
 
 # ---------------------------------------------------------------- CPU oracle leg
@@ -83,7 +90,7 @@ import oracle
 from workloads import make_workload
 from workloads.fields import field_at_cells_np
 args = json.loads(sys.argv[1])
-w = make_workload(args["workload"])
+w = make_workload(args["workload"], **args["kw"])
 g = oracle.Grid(w.faces, w.periodic)
 b0, b1 = args["bodies"]
 f0, f1 = int(w.body_faces[b0]), int(w.body_faces[b1])
@@ -110,12 +117,13 @@ print(json.dumps({"markers": int(f1 - f0), "times": times}))
 """
 
 
-def run_oracle_sample(name, method, bodies, reps, out):
+def run_oracle_sample(name, method, bodies, reps, out, kw=None):
     env = dict(os.environ)
     env["MLS_ROOT"] = ROOT
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    args = json.dumps({"workload": name, "method": method, "bodies": bodies, "reps": reps, "out": out})
+    args = json.dumps({"workload": name, "method": method, "bodies": bodies, "reps": reps, "out": out,
+                       "kw": kw or {}})
     r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, args], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
@@ -211,7 +219,7 @@ def run_ours(a, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload(a.workload)
+    w = workload(a.workload, a.grid, a.bodies)
     real = w.real
     tdt = torch.float32 if real == "f32" else torch.float64
     rs = 4 if real == "f32" else 8
@@ -247,9 +255,16 @@ def run_ours(a, rank, world, local):
     touched = int(torch.count_nonzero(f[0]).item())
     u_cells = touched / M
 
-    def timed(method, steps, warmup, per_kernel):
-        for _ in range(warmup):
+    def timed(method, steps, warmup, per_kernel, min_warm_s=0.0):
+        # At least `warmup` untimed steps, and at least min_warm_s of load so the
+        # clock sampler sees the GPU busy around the timed region.
+        t0 = time.perf_counter()
+        done = 0
+        while done < warmup or time.perf_counter() - t0 < min_warm_s:
             step(method)
+            done += 1
+            if done % 16 == 0:
+                torch.cuda.synchronize()
         torch.cuda.synchronize()
         if per_kernel:
             ctx.read_timing()
@@ -274,7 +289,7 @@ def run_ours(a, rank, world, local):
     # headline: plain timed region (no per-kernel events), clocks sampled during it
     clk = ClockSampler(local)
     clk.start()
-    ms, _ = timed(a.method, a.steps, a.warmup, False)
+    ms, _ = timed(a.method, a.steps, a.warmup, False, min_warm_s=1.5)
     clocks = clk.stop()
     total_ms = sum(ms)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -338,7 +353,8 @@ def run_ours(a, rank, world, local):
         nb = min(a.sample_bodies, len(w.body_faces) - 1)
         with tempfile.TemporaryDirectory() as td:
             out = os.path.join(td, "s.npz")
-            r = run_oracle_sample(a.workload, a.method, [0, nb], 1, out)
+            kw = {k: v for k, v in (("n", a.grid), ("n_bodies", a.bodies)) if v is not None}
+            r = run_oracle_sample(a.workload, a.method, [0, nb], 1, out, kw)
             ref = np.load(out)
             k = ref["phi"].shape[0]
             v = ctx.view(T)
@@ -364,7 +380,9 @@ def run_ours(a, rank, world, local):
         "metric": METRIC, "value": value, "unit": "markers/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": real, "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[a.workload], "markers_per_gpu": M, "method": a.method,
+        "config": {"workload": WORKLOAD_TEXT[a.workload] if a.grid is None and a.bodies is None else
+                   f"{a.workload} variant: {len(w.body_faces) - 1} bodies, {w.n[0]}x{w.n[1]}x{w.n[2]} grid",
+                   "markers_per_gpu": M, "method": a.method,
                    "grid": list(w.n), "l2": "flushed by a 256 MiB write before every timed step",
                    "step": "marker_prep + build_transfer + interpolate + spread",
                    "touched_cells_per_marker": round(u_cells, 4)},
