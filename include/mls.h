@@ -179,6 +179,35 @@ int mls_transfer_status(const mls_transfer* T, void* stream, mls_status* out);
  * class = home index along the one non-uniform axis (0 when all are uniform). */
 int mls_fast_table(mls_ctx* ctx, void* stream, const void** table, int64_t* n_classes, int32_t* n_sub);
 
+/* Build without allocating.  The paper has no counterpart: this is a
+ * convenience of the library for callers that cannot call cudaMalloc when
+ * they build, for example a flow solver whose device memory all comes from
+ * its own pool, or a time step in which a device allocation would
+ * synchronise the whole device.  It computes exactly what
+ * mls_build_transfer computes, with these differences:
+ *   - the results go to caller-owned device buffers laid out like
+ *     mls_transfer_arrays with capacity ld_phi (>= M):
+ *       phi real[27][ld_phi], c real[ld_phi], home int32[ld_phi], perm int32[ld_phi];
+ *   - the tile-sort workspace lives in one static device array of
+ *     MLS_NOALLOC_SCRATCH_BYTES (about 4.2 MB) that every GPU which loads
+ *     the library holds until the process exits;
+ *   - limits: M <= MLS_NOALLOC_MAX_MARKERS and the context's spreading-tile
+ *     count + 1 <= MLS_NOALLOC_MAX_BINS, else MLS_ERR_CAPACITY;
+ *   - MLS_FAST needs the context's fast-MLS table to exist already (build it
+ *     at set-up with mls_fast_table, which allocates), else MLS_ERR_UNSUPPORTED;
+ *   - no counters are returned: dropped markers are those with home = -1.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other contexts on the same device)
+ * race and corrupt each other's results, so serialise them.  The context's
+ * device must be current.  Calls no cudaMalloc or cudaFree. */
+#define MLS_NOALLOC_MAX_MARKERS 262144
+#define MLS_NOALLOC_MAX_BINS 266240
+#define MLS_NOALLOC_SCRATCH_BYTES 4227840
+int mls_build_transfer_noalloc(mls_ctx* ctx, const void* x, const void* area, int64_t M, int32_t method,
+                               void* phi, void* c, int32_t* home, int32_t* perm, int64_t ld_phi, void* stream);
+
 /* Per-kernel CUDA-event timing on the launching stream (off by default).
  * mls_timing_read synchronises the device, returns up to `max` accumulated
  * records in `out`, their count in `n`, and resets the accumulators. */

@@ -23,6 +23,9 @@ MLS_F64 = 0
 MLS_F32 = 1
 MLS_BF16 = 2
 
+MLS_NOALLOC_MAX_MARKERS = 262144
+MLS_NOALLOC_MAX_BINS = 266240
+
 
 class mls_grid(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("periodic", C.c_int32 * 3), ("faces", C.POINTER(C.c_double) * 3)]
@@ -63,6 +66,9 @@ SIGNATURES = {
     "mls_transfer_status": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mls_status)]),
     "mls_fast_table": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int32)]),
+    "mls_build_transfer_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                             C.c_void_p]),
     "mls_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "mls_timing_read": (C.c_int, [C.c_void_p, C.POINTER(mls_kernel_time), C.c_int32, C.POINTER(C.c_int32)]),
     "mls_strerror": (C.c_char_p, [C.c_int32]),

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmls_gb300.so")
-SOURCES = ["mls_api.cu", "k_prep_sort.cu", "k_build.cu", "k_transfer.cu"]
+SOURCES = ["mls_api.cu", "k_prep_sort.cu", "k_build.cu", "k_transfer.cu", "mls_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
