@@ -189,7 +189,7 @@ int mls_fast_table(mls_ctx* ctx, void* stream, const void** table, int64_t* n_cl
  *     mls_transfer_arrays with capacity ld_phi (>= M):
  *       phi real[27][ld_phi], c real[ld_phi], home int32[ld_phi], perm int32[ld_phi];
  *   - the tile-sort workspace lives in one static device array of
- *     MLS_NOALLOC_SCRATCH_BYTES (about 4.2 MB) that every GPU which loads
+ *     MLS_NOALLOC_SCRATCH_BYTES (about 5.3 MB) that every GPU which loads
  *     the library holds until the process exits;
  *   - limits: M <= MLS_NOALLOC_MAX_MARKERS and the context's spreading-tile
  *     count + 1 <= MLS_NOALLOC_MAX_BINS, else MLS_ERR_CAPACITY;
@@ -204,7 +204,7 @@ int mls_fast_table(mls_ctx* ctx, void* stream, const void** table, int64_t* n_cl
  * device must be current.  Calls no cudaMalloc or cudaFree. */
 #define MLS_NOALLOC_MAX_MARKERS 262144
 #define MLS_NOALLOC_MAX_BINS 266240
-#define MLS_NOALLOC_SCRATCH_BYTES 4227840
+#define MLS_NOALLOC_SCRATCH_BYTES 5293312
 int mls_build_transfer_noalloc(mls_ctx* ctx, const void* x, const void* area, int64_t M, int32_t method,
                                void* phi, void* c, int32_t* home, int32_t* perm, int64_t ld_phi, void* stream);
 

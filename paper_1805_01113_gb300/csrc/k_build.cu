@@ -57,14 +57,13 @@ __device__ __forceinline__ bool marker_setup(const BuildArgs<R>& a, int64_t j, i
 }
 
 template <typename R>
-__device__ __forceinline__ void marker_store(const BuildArgs<R>& a, int64_t j, const int h[3],
-                                             const AxisNodes<R> s[3], const R phi[27], R ar) {
-#pragma unroll
-  for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = phi[k];
-  a.c[j] = scale_factor(s, phi, ar);
+__device__ __forceinline__ void marker_finish(const BuildArgs<R>& a, int64_t j, const int h[3],
+                                              const AxisNodes<R> s[3], const ScaleSums<R>& sums, R ar) {
+  a.c[j] = sums.vol != R(0) ? sums.scale(s, ar) : R(0);
   a.home[j] = (h[2] * a.g.ax[1].n + h[1]) * a.g.ax[0].n + h[0];
 }
 
+// Exact-MLS build (Eqs. 3-6, 8): phi is written node by node as it is formed.
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_build_exact(BuildArgs<R> a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,27 +72,36 @@ __global__ void __launch_bounds__(kBlock) k_build_exact(BuildArgs<R> a) {
   R p[3], ar;
   AxisNodes<R> s[3];
   if (!marker_setup(a, j, h, p, s, ar)) return;
-  R phi[27];
+  R w[3][3], y[4];
   R cond = R(0);
   const bool want_cond = sizeof(R) == 4 && a.cond_max > 0.0;
-  bool good = shape_exact<R>(s, a.inv_eps2, a.refine, phi, want_cond ? &cond : nullptr);
+  bool good = exact_solve<R>(s, a.inv_eps2, a.refine, w, y, want_cond ? &cond : nullptr);
+  ScaleSums<R> sums;
   if (sizeof(R) == 4 && (!good || (want_cond && (double)cond > a.cond_max))) {
     // Ill-conditioned (or not numerically SPD) in single precision: redo the
     // marker in double and round the result.
     AxisNodes<double> sd[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) sd[d] = axis_nodes(a.gd.ax[d], h[d], (double)p[d]);
-    double phid[27];
-    good = shape_exact<double>(sd, a.inv_eps2_d, 0, phid, nullptr);
-#pragma unroll
-    for (int k = 0; k < 27; ++k) phi[k] = (R)phid[k];
+    double wd[3][3], yd[4];
+    good = exact_solve<double>(sd, a.inv_eps2_d, 0, wd, yd, nullptr);
+    if (good)
+      exact_emit(sd, wd, yd, [&](int q, int b, int c, double v) {
+        a.phi[(9 * c + 3 * b + q) * a.cap + j] = (R)v;
+        sums.add(s, q, b, c, (R)v);
+      });
     atomicAdd(&a.status[2], 1ULL);
+  } else if (good) {
+    exact_emit(s, w, y, [&](int q, int b, int c, R v) {
+      a.phi[(9 * c + 3 * b + q) * a.cap + j] = v;
+      sums.add(s, q, b, c, v);
+    });
   }
   if (!good) {
 #pragma unroll
-    for (int k = 0; k < 27; ++k) phi[k] = R(0);
+    for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = R(0);
   }
-  marker_store(a, j, h, s, phi, ar);
+  marker_finish(a, j, h, s, sums, ar);
 }
 
 // Fast-MLS: the marker's position in its home cell picks the enclosing
@@ -141,22 +149,30 @@ __global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
   }
   const R inv = R(1) / sum;
   const int cl = a.class_axis >= 0 ? h[a.class_axis] : 0;
-  const R* T = a.table + (int64_t)cl * n * n * n * 27;
-  const R* rows[8];
+  const R* T = a.table + (int64_t)cl * n * n * n * 27 +
+               (int64_t)(((sc[2] * n) + sc[1]) * n + sc[0]) * 27;
+  // Corner q sits at sub-node offset (q&1, (q>>1)&1, q>>2) from the sub-cell origin.
+  int64_t roff[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     alpha[q] *= inv;
-    rows[q] = T + (int64_t)((((sc[2] + (q >> 2)) * n) + (sc[1] + ((q >> 1) & 1))) * n + (sc[0] + (q & 1))) * 27;
+    roff[q] = (int64_t)((((q >> 2) * n) + ((q >> 1) & 1)) * n + (q & 1)) * 27;
   }
-  R phi[27];
+  ScaleSums<R> sums;
 #pragma unroll
-  for (int k = 0; k < 27; ++k) {
-    R v = R(0);
+  for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v += alpha[q] * __ldg(&rows[q][k]);
-    phi[k] = v;
-  }
-  marker_store(a, j, h, s, phi, ar);
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) {
+        const int k = 9 * c + 3 * b + q3;
+        R v = R(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v += alpha[q] * __ldg(T + roff[q] + k);
+        a.phi[k * a.cap + j] = v;
+        sums.add(s, q3, b, c, v);
+      }
+  marker_finish(a, j, h, s, sums, ar);
 }
 
 // Table of exact shape functions at the sub-Eulerian nodes -1/2 + i/(n-1)

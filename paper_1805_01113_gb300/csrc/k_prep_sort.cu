@@ -150,57 +150,83 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int* t
   return incl - v + warp_tot[wid];
 }
 
+// Per scan tile of 4096 bins: the number of markers and the number of
+// non-empty spreading tiles (the last bin, dropped markers, is not a tile).
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __restrict__ counts, int nbins,
-                                                              int32_t* __restrict__ tile_sums) {
+                                                              int ntiles, int32_t* __restrict__ tile_sums) {
   __shared__ int warp_tot[32];
   __shared__ int total;
   const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
-  int v = 0;
+  int v = 0, ne = 0;
 #pragma unroll
   for (int q = 0; q < kScanPer; ++q)
-    if (base + q < nbins) v += counts[base + q];
+    if (base + q < nbins) {
+      const int cq = counts[base + q];
+      v += cq;
+      ne += (cq > 0 && base + q < nbins - 1) ? 1 : 0;
+    }
   block_exclusive_scan(v, warp_tot, &total);
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+  __syncthreads();
+  block_exclusive_scan(ne, warp_tot, &total);
+  if (threadIdx.x == 0) tile_sums[ntiles + blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_tiles(int32_t* __restrict__ tile_sums, int ntiles) {
+// Exclusive scan of both per-tile sums (one block); the total of the second
+// is the length of the non-empty tile list.
+__global__ void __launch_bounds__(1024) k_scan_tiles(int32_t* __restrict__ tile_sums, int ntiles,
+                                                     int32_t* __restrict__ n_items) {
   __shared__ int warp_tot[32];
   __shared__ int total;
   constexpr int per = kScanMaxTiles / 1024;
-  int v[per];
-  int s = 0;
+  for (int part = 0; part < 2; ++part) {
+    int32_t* ts = tile_sums + part * ntiles;
+    int v[per];
+    int s = 0;
 #pragma unroll
-  for (int q = 0; q < per; ++q) {
-    const int i = threadIdx.x * per + q;
-    v[q] = i < ntiles ? tile_sums[i] : 0;
-    s += v[q];
-  }
-  int run = block_exclusive_scan(s, warp_tot, &total);
+    for (int q = 0; q < per; ++q) {
+      const int i = threadIdx.x * per + q;
+      v[q] = i < ntiles ? ts[i] : 0;
+      s += v[q];
+    }
+    int run = block_exclusive_scan(s, warp_tot, &total);
 #pragma unroll
-  for (int q = 0; q < per; ++q) {
-    const int i = threadIdx.x * per + q;
-    if (i < ntiles) tile_sums[i] = run;
-    run += v[q];
+    for (int q = 0; q < per; ++q) {
+      const int i = threadIdx.x * per + q;
+      if (i < ntiles) ts[i] = run;
+      run += v[q];
+    }
+    if (part == 1 && threadIdx.x == 0) *n_items = total;
+    __syncthreads();
   }
 }
 
+// Bin offsets (exclusive prefix of the counts) and the ascending list of
+// non-empty spreading tiles.
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* __restrict__ counts, int nbins,
-                                                             const int32_t* __restrict__ tile_sums,
-                                                             int32_t* __restrict__ offsets) {
+                                                             int ntiles, const int32_t* __restrict__ tile_sums,
+                                                             int32_t* __restrict__ offsets,
+                                                             int32_t* __restrict__ items) {
   __shared__ int warp_tot[32];
   __shared__ int total;
   const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
   int v[kScanPer];
-  int s = 0;
+  int s = 0, ne = 0;
 #pragma unroll
   for (int q = 0; q < kScanPer; ++q) {
     v[q] = base + q < nbins ? counts[base + q] : 0;
     s += v[q];
+    ne += (v[q] > 0 && base + q < nbins - 1) ? 1 : 0;
   }
   int run = block_exclusive_scan(s, warp_tot, &total) + tile_sums[blockIdx.x];
+  __syncthreads();
+  int pos = block_exclusive_scan(ne, warp_tot, &total) + tile_sums[ntiles + blockIdx.x];
 #pragma unroll
   for (int q = 0; q < kScanPer; ++q) {
-    if (base + q < nbins) offsets[base + q] = run;
+    if (base + q < nbins) {
+      offsets[base + q] = run;
+      if (v[q] > 0 && base + q < nbins - 1) items[pos++] = base + q;
+    }
     run += v[q];
   }
 }
@@ -208,13 +234,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* __re
 cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx) {
   const int ntiles = (nbins + kScanTile - 1) / kScanTile;
   int slot = timer_begin(ctx, "scan_reduce", s);
-  k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, T->tile_sums);
+  k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, ntiles, T->tile_sums);
   timer_end(ctx, slot, s);
   slot = timer_begin(ctx, "scan_tiles", s);
-  k_scan_tiles<<<1, 1024, 0, s>>>(T->tile_sums, ntiles);
+  k_scan_tiles<<<1, 1024, 0, s>>>(T->tile_sums, ntiles, T->n_items);
   timer_end(ctx, slot, s);
   slot = timer_begin(ctx, "scan_apply", s);
-  k_scan_apply<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, T->tile_sums, T->offsets);
+  k_scan_apply<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, ntiles, T->tile_sums, T->offsets, T->items);
   timer_end(ctx, slot, s);
   return cudaGetLastError();
 }

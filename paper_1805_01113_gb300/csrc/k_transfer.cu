@@ -13,13 +13,6 @@ template <typename R, typename FT> __device__ __forceinline__ R load_field(const
 }
 template <> __device__ __forceinline__ double load_field<double, double>(const double* p) { return __ldg(p); }
 
-template <typename R, typename FT> __device__ __forceinline__ void add_field(FT* p, R v);
-template <> __device__ __forceinline__ void add_field<double, double>(double* p, double v) { atomicAdd(p, v); }
-template <> __device__ __forceinline__ void add_field<float, float>(float* p, float v) { atomicAdd(p, v); }
-template <> __device__ __forceinline__ void add_field<float, __nv_bfloat16>(__nv_bfloat16* p, float v) {
-  atomicAdd(p, __float2bfloat16_rn(v));
-}
-
 struct Dims {
   int n[3];
   int periodic[3];
@@ -79,82 +72,258 @@ __global__ void __launch_bounds__(kBlock) k_interp(Dims D, const R* __restrict__
   U[2 * M + m] = s2;
 }
 
-// f_k += sum_l c_l phi_k^l F_l (text after Eq. 7).  A block takes 256
-// consecutive stored markers, which are grouped by spreading tile.  For each
-// run of markers of one tile it zeroes a shared-memory accumulator covering
-// the tile plus a one-cell halo, adds the 81 contributions of every marker
-// with shared-memory atomics, then adds each non-zero accumulator cell to f
-// with one global atomic per component.
-template <typename R, typename FT>
-__global__ void __launch_bounds__(kBlock) k_spread(Dims D, Tiles tl, const R* __restrict__ phi,
-                                                   const R* __restrict__ cl, const int32_t* __restrict__ home,
-                                                   const int32_t* __restrict__ perm, int64_t M, int64_t cap,
-                                                   const R* __restrict__ F, FT* __restrict__ f) {
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+template <typename R, typename FT> __device__ __forceinline__ void add_field(FT* p, R v);
+template <> __device__ __forceinline__ void add_field<double, double>(double* p, double v) { atomicAdd(p, v); }
+template <> __device__ __forceinline__ void add_field<float, float>(float* p, float v) { atomicAdd(p, v); }
+template <> __device__ __forceinline__ void add_field<float, __nv_bfloat16>(__nv_bfloat16* p, float v) {
+  atomicAdd(p, __float2bfloat16_rn(v));
+}
+
+// Shared-memory layout of one spreading block (bytes), shared by host and device.
+struct SpreadSmem {
+  int acc, offs, total;
+  __host__ __device__ SpreadSmem(int rs, int lx, int ly, int lz, bool vec) {
+    const int xoff = vec ? 4 : 1;
+    const int ACC = ((1 << lx) + 2 * xoff) * ((1 << ly) + 2) * ((1 << lz) + 2);
+    acc = 0;
+    offs = acc + 3 * ACC * rs;                     // 27 node offsets inside the accumulator
+    total = (offs + 27 * 4 + 15) & ~15;
+  }
+};
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = red[0];
+#pragma unroll
+  for (int w = 1; w < kSpreadThreads / 32; ++w) m = fmaxf(m, red[w]);
+  return m;
+}
+
+// round-to-nearest integer of x for |x| <= 2^22: adding 1.5 * 2^23 leaves the
+// integer in the low mantissa bits.
+__device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
+
+// f_k += sum_l c_l phi_k^l F_l (text after Eq. 7), single precision.
+// Persistent blocks walk the list of non-empty spreading tiles, taking up to
+// 128 markers of a tile at a time (one per thread).  For such a chunk a block
+// finds the largest |c_l F_l|, scales contributions by a power of two so that
+// any |phi| <= 1 term is at most 2^22 units, rounds them to integers and adds
+// them into a shared-memory accumulator (tile plus one-cell halo) with native
+// 32-bit integer atomics; a cell's sum stays below 128 * 2^22 = 2^29.  A term
+// outside that range (|phi| > 1) is added to f directly with a float atomic.
+// Each non-zero cell is then converted back and added to f with one global
+// atomic per component.  The quantum is 2^-21 of the chunk's largest |c F|.
+// With VEC the accumulator rows are padded to 4-aligned x groups of the field
+// ([ox-4, ox+2^l+4)) and flushed with 16-byte vector atomics (zero lanes of a
+// group add nothing).  A chunk with non-finite forces is added directly.
+template <typename FT, bool VEC>
+__global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, const float* __restrict__ phi,
+                                                           const float* __restrict__ cl,
+                                                           const int32_t* __restrict__ home,
+                                                           const int32_t* __restrict__ perm,
+                                                           const int32_t* __restrict__ items,
+                                                           const int32_t* __restrict__ n_items_p,
+                                                           const int32_t* __restrict__ offsets,
+                                                           const int32_t* __restrict__ counts, int64_t M, int64_t cap,
+                                                           const float* __restrict__ F, FT* __restrict__ f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* acc = reinterpret_cast<R*>(smem_raw);
-  __shared__ int s_key[kBlock];
+  const SpreadSmem L(4, tl.l[0], tl.l[1], tl.l[2], VEC);
+  int* acc = reinterpret_cast<int*>(smem_raw + L.acc);
+  int* s_off = reinterpret_cast<int*>(smem_raw + L.offs);
+  __shared__ float s_red[kSpreadThreads / 32];
+  constexpr int XOFF = VEC ? 4 : 1;
+  const int AX = (1 << tl.l[0]) + 2 * XOFF, AY = (1 << tl.l[1]) + 2, AZ = (1 << tl.l[2]) + 2;
+  const int ACC = AX * AY * AZ;
+  const int tid = threadIdx.x;
+  const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
+  const int n_items = *n_items_p;
+  if (tid < 27) s_off[tid] = ((tid / 9) * AY + (tid / 3) % 3) * AX + tid % 3;
+
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int b = items[it];
+    const int start = offsets[b], cnt = counts[b];
+    const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
+    const int ox = bx << tl.l[0], oy = by << tl.l[1], oz = bz << tl.l[2];
+    for (int j0 = start; j0 < start + cnt; j0 += kSpreadThreads) {
+      const int64_t j = j0 + tid;
+      const bool act = j < start + cnt;
+      int i[3] = {0, 0, 0};
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if (act) {
+        decode_home(home[j], D, i);
+        const int64_t m = perm[j];
+        const float c = cl[j];
+        v0 = c * F[m];
+        v1 = c * F[M + m];
+        v2 = c * F[2 * M + m];
+      }
+      for (int e = tid; e < 3 * ACC / 4; e += kSpreadThreads)
+        reinterpret_cast<int4*>(acc)[e] = make_int4(0, 0, 0, 0);
+      const float vmax = block_max(fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2))), s_red);  // barrier inside
+      if (vmax == 0.f) {
+        __syncthreads();
+        continue;
+      }
+      if (!isfinite(vmax)) {
+        if (act) {
+          const float v[3] = {v0, v1, v2};
+          for (int k = 0; k < 27; ++k) {
+            const int gx = wrap(i[0] + k % 3 - 1, D.n[0], D.periodic[0]);
+            const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);
+            const int gz = wrap(i[2] + k / 9 - 1, D.n[2], D.periodic[2]);
+            const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
+            const float p = phi[k * cap + j];
+            for (int q = 0; q < 3; ++q) add_field<float, FT>(f + q * N + o, p * v[q]);
+          }
+        }
+        __syncthreads();
+        continue;
+      }
+      int ex;
+      frexpf(vmax, &ex);                             // vmax < 2^ex
+      const float scale = ldexpf(1.f, 22 - ex);      // |p v| * scale <= 2^22 for |p| <= 1
+      const float inv_scale = ldexpf(1.f, ex - 22);
+      if (act) {
+        const float s0 = v0 * scale, s1 = v1 * scale, s2 = v2 * scale;
+        const int base = ((i[2] - oz) * AY + (i[1] - oy)) * AX + (i[0] - ox) + XOFF - 1;
+        float p[27];
+#pragma unroll
+        for (int k = 0; k < 27; ++k) p[k] = phi[k * cap + j];
+#pragma unroll
+        for (int k = 0; k < 27; ++k) {
+          const int li = base + s_off[k];
+          const float x0 = p[k] * s0, x1 = p[k] * s1, x2 = p[k] * s2;
+          if (fmaxf(fabsf(x0), fmaxf(fabsf(x1), fabsf(x2))) <= 4194304.0f) {
+            atomicAdd(&acc[li], round_small(x0));
+            atomicAdd(&acc[ACC + li], round_small(x1));
+            atomicAdd(&acc[2 * ACC + li], round_small(x2));
+          } else {
+            const int gx = wrap(i[0] + k % 3 - 1, D.n[0], D.periodic[0]);
+            const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);
+            const int gz = wrap(i[2] + k / 9 - 1, D.n[2], D.periodic[2]);
+            const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
+            add_field<float, FT>(f + o, p[k] * v0);
+            add_field<float, FT>(f + N + o, p[k] * v1);
+            add_field<float, FT>(f + 2 * N + o, p[k] * v2);
+          }
+        }
+      }
+      __syncthreads();
+      if (VEC) {
+        const int G = AX / 4;
+        for (int g = tid; g < G * AY * AZ; g += kSpreadThreads) {
+          const int q = g % G, row = g / G;
+          const int ey = row % AY, ez = row / AY;
+          const int e = row * AX + 4 * q;
+          const int4 a0 = *reinterpret_cast<const int4*>(&acc[e]);
+          const int4 a1 = *reinterpret_cast<const int4*>(&acc[ACC + e]);
+          const int4 a2 = *reinterpret_cast<const int4*>(&acc[2 * ACC + e]);
+          const bool n0 = (a0.x | a0.y | a0.z | a0.w) != 0;
+          const bool n1 = (a1.x | a1.y | a1.z | a1.w) != 0;
+          const bool n2 = (a2.x | a2.y | a2.z | a2.w) != 0;
+          if (!(n0 || n1 || n2)) continue;
+          int gx = ox - XOFF + 4 * q;
+          if (gx < 0 || gx >= D.n[0]) {
+            if (!D.periodic[0]) continue;
+            gx = gx < 0 ? gx + D.n[0] : gx - D.n[0];
+            if (gx < 0 || gx >= D.n[0]) continue;      // padding beyond one period holds no sums
+          }
+          const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
+          const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
+          float* fo = reinterpret_cast<float*>(f) + ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
+          if (n0)
+            red_add_v4(fo, a0.x * inv_scale, a0.y * inv_scale, a0.z * inv_scale, a0.w * inv_scale);
+          if (n1)
+            red_add_v4(fo + N, a1.x * inv_scale, a1.y * inv_scale, a1.z * inv_scale, a1.w * inv_scale);
+          if (n2)
+            red_add_v4(fo + 2 * N, a2.x * inv_scale, a2.y * inv_scale, a2.z * inv_scale, a2.w * inv_scale);
+        }
+      } else {
+        for (int e = tid; e < ACC; e += kSpreadThreads) {
+          const int a0 = acc[e], a1 = acc[ACC + e], a2 = acc[2 * ACC + e];
+          if ((a0 | a1 | a2) != 0) {
+            const int ex2 = e % AX, ey = (e / AX) % AY, ez = e / (AX * AY);
+            const int gx = wrap(ox - XOFF + ex2, D.n[0], D.periodic[0]);
+            const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
+            const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
+            const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
+            if (a0) add_field<float, FT>(f + o, a0 * inv_scale);
+            if (a1) add_field<float, FT>(f + N + o, a1 * inv_scale);
+            if (a2) add_field<float, FT>(f + 2 * N + o, a2 * inv_scale);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Double-precision spreading: the same tile walk with double shared-memory
+// atomics (used for the small double-precision workloads).
+__global__ void __launch_bounds__(kSpreadThreads) k_spread_f64(Dims D, Tiles tl, const double* __restrict__ phi,
+                                                               const double* __restrict__ cl,
+                                                               const int32_t* __restrict__ home,
+                                                               const int32_t* __restrict__ perm,
+                                                               const int32_t* __restrict__ items,
+                                                               const int32_t* __restrict__ n_items_p,
+                                                               const int32_t* __restrict__ offsets,
+                                                               const int32_t* __restrict__ counts, int64_t M,
+                                                               int64_t cap, const double* __restrict__ F,
+                                                               double* __restrict__ f) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* acc = reinterpret_cast<double*>(smem_raw);
   const int AX = (1 << tl.l[0]) + 2, AY = (1 << tl.l[1]) + 2, AZ = (1 << tl.l[2]) + 2;
   const int ACC = AX * AY * AZ;
   const int tid = threadIdx.x;
-  const int64_t j = (int64_t)blockIdx.x * kBlock + tid;
-
-  int key = INT_MAX;
-  int i[3] = {0, 0, 0};
-  R v0 = R(0), v1 = R(0), v2 = R(0);
-  if (j < M) {
-    const int32_t h = home[j];
-    if (h >= 0) {
-      decode_home(h, D, i);
-      key = (((i[2] >> tl.l[2]) * tl.nb[1]) + (i[1] >> tl.l[1])) * tl.nb[0] + (i[0] >> tl.l[0]);
-      const int64_t m = perm[j];
-      const R c = cl[j];
-      v0 = c * F[m];
-      v1 = c * F[M + m];
-      v2 = c * F[2 * M + m];
-    }
-  }
-  s_key[tid] = key;
-  __syncthreads();
   const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
-
-  int start = 0;
-  while (start < kBlock) {
-    const int cur = s_key[start];
-    if (cur == INT_MAX) break;
-    const int bx = cur % tl.nb[0], by = (cur / tl.nb[0]) % tl.nb[1], bz = cur / (tl.nb[0] * tl.nb[1]);
+  const int n_items = *n_items_p;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int b = items[it];
+    const int start = offsets[b], cnt = counts[b];
+    const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
     const int ox = bx << tl.l[0], oy = by << tl.l[1], oz = bz << tl.l[2];
-    for (int e = tid; e < 3 * ACC; e += kBlock) acc[e] = R(0);
+    for (int e = tid; e < 3 * ACC; e += kSpreadThreads) acc[e] = 0.0;
     __syncthreads();
-    if (key == cur) {
+    for (int j = start + tid; j < start + cnt; j += kSpreadThreads) {
+      int i[3];
+      decode_home(home[j], D, i);
+      const int64_t m = perm[j];
+      const double c = cl[j];
+      const double v0 = c * F[m], v1 = c * F[M + m], v2 = c * F[2 * M + m];
       const int lx = i[0] - ox, ly = i[1] - oy, lz = i[2] - oz;
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const R p = phi[(9 * c + 3 * b + a) * cap + j];
-            const int li = ((lz + c) * AY + (ly + b)) * AX + (lx + a);
+      for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+          for (int cx = 0; cx < 3; ++cx) {
+            const double p = phi[(9 * cz + 3 * cy + cx) * cap + j];
+            const int li = ((lz + cz) * AY + (ly + cy)) * AX + (lx + cx);
             atomicAdd(&acc[li], p * v0);
             atomicAdd(&acc[ACC + li], p * v1);
             atomicAdd(&acc[2 * ACC + li], p * v2);
           }
     }
     __syncthreads();
-    for (int e = tid; e < ACC; e += kBlock) {
-      const R a0 = acc[e], a1 = acc[ACC + e], a2 = acc[2 * ACC + e];
-      if (a0 != R(0) || a1 != R(0) || a2 != R(0)) {
+    for (int e = tid; e < ACC; e += kSpreadThreads) {
+      const double a0 = acc[e], a1 = acc[ACC + e], a2 = acc[2 * ACC + e];
+      if (a0 != 0.0 || a1 != 0.0 || a2 != 0.0) {
         const int ex = e % AX, ey = (e / AX) % AY, ez = e / (AX * AY);
         const int gx = wrap(ox - 1 + ex, D.n[0], D.periodic[0]);
         const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
         const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
         const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
-        if (a0 != R(0)) add_field<R, FT>(f + o, a0);
-        if (a1 != R(0)) add_field<R, FT>(f + N + o, a1);
-        if (a2 != R(0)) add_field<R, FT>(f + 2 * N + o, a2);
+        if (a0 != 0.0) atomicAdd(f + o, a0);
+        if (a1 != 0.0) atomicAdd(f + N + o, a1);
+        if (a2 != 0.0) atomicAdd(f + 2 * N + o, a2);
       }
     }
-    start += __syncthreads_count(key == cur);
+    __syncthreads();
   }
 }
 
@@ -167,20 +336,42 @@ static Dims dims_of(const mls_ctx* ctx) {
   return D;
 }
 
-size_t spread_smem_bytes(const mls_ctx* ctx) {
-  const size_t acc = (size_t)((1 << ctx->tiles.l[0]) + 2) * ((1 << ctx->tiles.l[1]) + 2) *
-                     ((1 << ctx->tiles.l[2]) + 2);
-  return 3 * acc * (ctx->opt.real == MLS_F64 ? sizeof(double) : sizeof(float));
+// The vector flush needs float fields, 4-aligned tile columns (l_x >= 2) and
+// an x extent that is a multiple of 4 (so a wrapped group stays aligned).
+static bool spread_vec(const mls_ctx* ctx) {
+  return ctx->opt.field == MLS_F32 && ctx->tiles.l[0] >= 2 && ctx->n[0] % 4 == 0;
 }
 
-cudaError_t spread_configure(const mls_ctx* ctx) {
+size_t spread_smem_bytes(const mls_ctx* ctx) {
+  const int rs = ctx->opt.real == MLS_F64 ? 8 : 4;
+  return (size_t)SpreadSmem(rs, ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2], spread_vec(ctx)).total;
+}
+
+template <typename K>
+static cudaError_t configure_kernel(mls_ctx* ctx, K kernel, int smem) {
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSpreadThreads, smem);
+  if (e != cudaSuccess) return e;
+  ctx->spread_grid = (per_sm > 0 ? per_sm : 1) * sms;
+  return cudaSuccess;
+}
+
+cudaError_t spread_configure(mls_ctx* ctx) {
   const int smem = (int)spread_smem_bytes(ctx);
-  if (smem <= 48 * 1024) return cudaSuccess;
-  if (ctx->opt.real == MLS_F64)
-    return cudaFuncSetAttribute(k_spread<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (ctx->opt.field == MLS_F32)
-    return cudaFuncSetAttribute(k_spread<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return cudaFuncSetAttribute(k_spread<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (ctx->opt.real == MLS_F64) return configure_kernel(ctx, k_spread_f64, smem);
+  if (ctx->opt.field == MLS_BF16) return configure_kernel(ctx, k_spread<__nv_bfloat16, false>, smem);
+  if (spread_vec(ctx)) {
+    // The scalar variant also runs when f is not 16-byte aligned (same layout size or smaller).
+    cudaError_t e = configure_kernel(ctx, k_spread<float, false>, smem);
+    if (e != cudaSuccess) return e;
+    return configure_kernel(ctx, k_spread<float, true>, smem);
+  }
+  return configure_kernel(ctx, k_spread<float, false>, smem);
 }
 
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s) {
@@ -199,22 +390,22 @@ cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void*
   return cudaGetLastError();
 }
 
+template <typename FT, bool VEC>
+static void launch_spread_one(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s) {
+  k_spread<FT, VEC><<<ctx->spread_grid, kSpreadThreads, spread_smem_bytes(ctx), s>>>(
+      dims_of(ctx), ctx->tiles, (const float*)T->phi, (const float*)T->c, T->home, T->perm, T->items, T->n_items,
+      T->offsets, T->counts, T->M, T->cap, (const float*)F, (FT*)f);
+}
+
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s) {
   if (T->M == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((T->M + kBlock - 1) / kBlock);
-  const Dims D = dims_of(ctx);
-  const size_t smem = spread_smem_bytes(ctx);
   if (ctx->opt.real == MLS_F64)
-    k_spread<double, double><<<grid, kBlock, smem, s>>>(D, ctx->tiles, (const double*)T->phi, (const double*)T->c,
-                                                        T->home, T->perm, T->M, T->cap, (const double*)F,
-                                                        (double*)f);
-  else if (ctx->opt.field == MLS_F32)
-    k_spread<float, float><<<grid, kBlock, smem, s>>>(D, ctx->tiles, (const float*)T->phi, (const float*)T->c,
-                                                      T->home, T->perm, T->M, T->cap, (const float*)F, (float*)f);
-  else
-    k_spread<float, __nv_bfloat16><<<grid, kBlock, smem, s>>>(D, ctx->tiles, (const float*)T->phi,
-                                                              (const float*)T->c, T->home, T->perm, T->M, T->cap,
-                                                              (const float*)F, (__nv_bfloat16*)f);
+    k_spread_f64<<<ctx->spread_grid, kSpreadThreads, spread_smem_bytes(ctx), s>>>(
+        dims_of(ctx), ctx->tiles, (const double*)T->phi, (const double*)T->c, T->home, T->perm, T->items,
+        T->n_items, T->offsets, T->counts, T->M, T->cap, (const double*)F, (double*)f);
+  else if (ctx->opt.field == MLS_BF16) launch_spread_one<__nv_bfloat16, false>(ctx, T, F, f, s);
+  else if (spread_vec(ctx) && (reinterpret_cast<uintptr_t>(f) & 15) == 0) launch_spread_one<float, true>(ctx, T, F, f, s);
+  else launch_spread_one<float, false>(ctx, T, F, f, s);
   return cudaGetLastError();
 }
 

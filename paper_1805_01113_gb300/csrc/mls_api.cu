@@ -233,6 +233,8 @@ static void free_transfer(mls_transfer* T) {
   cudaFree(T->rank);
   cudaFree(T->counts);
   cudaFree(T->offsets);
+  cudaFree(T->items);
+  cudaFree(T->n_items);
   cudaFree(T->tile_sums);
   cudaFree(T->status);
   delete T;
@@ -260,7 +262,10 @@ int mls_transfer_create(mls_ctx* ctx, int64_t capacity, mls_transfer** out) {
       (e = cudaMalloc(&T->rank, (size_t)capacity * 4)) != cudaSuccess ||
       (e = cudaMalloc(&T->counts, (size_t)nbins * 4)) != cudaSuccess ||
       (e = cudaMalloc(&T->offsets, (size_t)nbins * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&T->tile_sums, (size_t)T->ntiles * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&T->items, (size_t)nbins * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&T->n_items, 4)) != cudaSuccess ||
+      (e = cudaMemset(T->n_items, 0, 4)) != cudaSuccess ||
+      (e = cudaMalloc(&T->tile_sums, (size_t)T->ntiles * 2 * 4)) != cudaSuccess ||
       (e = cudaMalloc(&T->status, 4 * sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMemset(T->status, 0, 4 * sizeof(unsigned long long))) != cudaSuccess) {
     free_transfer(T);

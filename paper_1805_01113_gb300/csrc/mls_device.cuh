@@ -195,54 +195,53 @@ __device__ __forceinline__ R cond1(const R a[10], const Chol4<R>& ch) {
   return an * inv_n;
 }
 
-// Exact-MLS shape functions of one marker from its per-axis node geometry.
+// Exact-MLS solve of one marker from its per-axis node geometry.
 //   Eq. 3: A = sum_k W_k p_k p_k^T with p_k = [1, xi_x, xi_y, xi_z] (marker-
 //          centred, home-width-scaled basis, an affine change of [1,x,y,z]
 //          under which Phi is invariant), W_k = exp(-|xi_k|^2/eps^2)
-//          evaluated as the product of three per-axis factors.
+//          evaluated as the product of three per-axis factors w[d][a].
 //   Eq. 6: Phi^T = p^T(x_l) A^-1 B = e_0^T A^-1 B, i.e. phi_k = W_k (y . p_k)
 //          with A y = e_0 (A is symmetric).
 // `refine` extra residual-correction steps are applied to y.  Returns false
 // if A is not numerically positive definite; `cond` (if non-null) receives
 // cond_1(A).
 template <typename R>
-__device__ __forceinline__ bool shape_exact(const AxisNodes<R> s[3], R inv_eps2, int refine, R phi[27],
+__device__ __forceinline__ bool exact_solve(const AxisNodes<R> s[3], R inv_eps2, int refine, R w[3][3], R y[4],
                                             R* cond) {
-  R w[3][3];
+  // Per-axis weights and moments S_m[d] = sum_a w[d][a] xi[d][a]^m.  The
+  // weight and the stencil are tensor products, so every entry of the
+  // 27-term sum of Eq. 3 factorises into a product of three of them, e.g.
+  // A_xy = sum_abc w_a w_b w_c xi_a xi_b = S1[x] S1[y] S0[z].
+  R S0[3], S1[3], S2[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d)
+  for (int d = 0; d < 3; ++d) {
+    S0[d] = S1[d] = S2[d] = R(0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) w[d][a] = dev_exp<R>(-(s[d].xi[a] * s[d].xi[a]) * inv_eps2);
-
+    for (int a = 0; a < 3; ++a) {
+      const R xi = s[d].xi[a];
+      const R wa = dev_exp<R>(-(xi * xi) * inv_eps2);
+      w[d][a] = wa;
+      S0[d] += wa;
+      S1[d] += wa * xi;
+      S2[d] += wa * xi * xi;
+    }
+  }
   R A[10];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) A[q] = R(0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const R W = w[0][a] * w[1][b] * w[2][c];
-        const R px = s[0].xi[a], py = s[1].xi[b], pz = s[2].xi[c];
-        const R Wx = W * px, Wy = W * py, Wz = W * pz;
-        A[0] += W;
-        A[1] += Wx;
-        A[2] += Wx * px;
-        A[3] += Wy;
-        A[4] += Wy * px;
-        A[5] += Wy * py;
-        A[6] += Wz;
-        A[7] += Wz * px;
-        A[8] += Wz * py;
-        A[9] += Wz * pz;
-      }
+  A[0] = S0[0] * S0[1] * S0[2];
+  A[1] = S1[0] * S0[1] * S0[2];
+  A[2] = S2[0] * S0[1] * S0[2];
+  A[3] = S0[0] * S1[1] * S0[2];
+  A[4] = S1[0] * S1[1] * S0[2];
+  A[5] = S0[0] * S2[1] * S0[2];
+  A[6] = S0[0] * S0[1] * S1[2];
+  A[7] = S1[0] * S0[1] * S1[2];
+  A[8] = S0[0] * S1[1] * S1[2];
+  A[9] = S0[0] * S0[1] * S2[2];
 
   Chol4<R> ch;
   ch.factor(A);
   if (!ch.ok) return false;
   const R e0[4] = {R(1), R(0), R(0), R(0)};
-  R y[4];
   ch.solve(e0, y);
   for (int it = 0; it < refine; ++it) {
     R Ay[4], r[4], dy[4];
@@ -258,42 +257,59 @@ __device__ __forceinline__ bool shape_exact(const AxisNodes<R> s[3], R inv_eps2,
     y[3] += dy[3];
   }
   if (cond) *cond = cond1(A, ch);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const R W = w[0][a] * w[1][b] * w[2][c];
-        phi[9 * c + 3 * b + a] = W * (y[0] + y[1] * s[0].xi[a] + y[2] * s[1].xi[b] + y[3] * s[2].xi[c]);
-      }
   return true;
 }
 
-// c_l of Eq. 8 with h_l = sum_k phi_k (Dx_k + Dy_k + Dz_k)/3 and
-// Delta V_l = A_l h_l; node widths are separable, so both sums run over
-// per-axis marginals of phi.
-template <typename R>
-__device__ __forceinline__ R scale_factor(const AxisNodes<R> s[3], const R phi[27], R area) {
-  R mx[3] = {R(0), R(0), R(0)}, my[3] = {R(0), R(0), R(0)}, mz[3] = {R(0), R(0), R(0)};
-  R vol = R(0);
+// Streams phi_k = W_k (y . p_k) = wx_a wy_b wz_c (y0 + y1 xi_x,a + y2 xi_y,b +
+// y3 xi_z,c) for k = 9c + 3b + a, with the (b, c) products formed once.
+template <typename R, typename Sink>
+__device__ __forceinline__ void exact_emit(const AxisNodes<R> s[3], const R w[3][3], const R y[4], Sink&& sink) {
+  R gx[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gx[a] = y[0] + y[1] * s[0].xi[a];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+    for (int b = 0; b < 3; ++b) {
+      const R wyz = w[1][b] * w[2][c];
+      const R gyz = y[2] * s[1].xi[b] + y[3] * s[2].xi[c];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const R p = phi[9 * c + 3 * b + a];
-        mx[a] += p;
-        my[b] += p;
-        mz[c] += p;
-        vol += p * (s[0].w[a] * s[1].w[b] * s[2].w[c]);
-      }
-  R hsum = R(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) hsum += mx[a] * s[0].w[a] + my[a] * s[1].w[a] + mz[a] * s[2].w[a];
-  const R h_l = hsum / R(3);
-  return (area * h_l) / vol;
+      for (int a = 0; a < 3; ++a) sink(a, b, c, (w[0][a] * wyz) * (gx[a] + gyz));
+    }
 }
+
+// All 27 exact shape functions (table path).
+template <typename R>
+__device__ __forceinline__ bool shape_exact(const AxisNodes<R> s[3], R inv_eps2, int refine, R phi[27],
+                                            R* cond) {
+  R w[3][3], y[4];
+  if (!exact_solve(s, inv_eps2, refine, w, y, cond)) return false;
+  exact_emit(s, w, y, [&](int a, int b, int c, R v) { phi[9 * c + 3 * b + a] = v; });
+  return true;
+}
+
+// Running sums for c_l of Eq. 8 while phi is streamed out.
+template <typename R>
+struct ScaleSums {
+  R mx[3], my[3], mz[3], vol;
+  __device__ __forceinline__ ScaleSums() {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) mx[q] = my[q] = mz[q] = R(0);
+    vol = R(0);
+  }
+  __device__ __forceinline__ void add(const AxisNodes<R> s[3], int a, int b, int c, R p) {
+    mx[a] += p;
+    my[b] += p;
+    mz[c] += p;
+    vol += p * (s[0].w[a] * s[1].w[b] * s[2].w[c]);
+  }
+  // c_l = A_l h_l / sum_k phi_k dV_k, h_l = sum_k phi_k (Dx_k + Dy_k + Dz_k)/3.
+  __device__ __forceinline__ R scale(const AxisNodes<R> s[3], R area) const {
+    R hsum = R(0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) hsum += mx[q] * s[0].w[q] + my[q] * s[1].w[q] + mz[q] * s[2].w[q];
+    return (area * (hsum / R(3))) / vol;
+  }
+};
 
 }  // namespace mls

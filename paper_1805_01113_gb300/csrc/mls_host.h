@@ -39,6 +39,8 @@ struct mls_ctx {
   void* table;
   int64_t n_classes;
   int class_axis;
+  // Persistent grid of the spreading kernel (blocks resident on the device).
+  int spread_grid;
   // Per-kernel timing.
   int timing;
   std::vector<mls_kernel_timer> timers;
@@ -59,7 +61,9 @@ struct mls_transfer {
   int32_t* rank;     // [cap] caller order: rank inside the bin
   int32_t* counts;   // [nbins]
   int32_t* offsets;  // [nbins]
-  int32_t* tile_sums;
+  int32_t* items;    // [nbins]: non-empty spreading tiles (bin ids, ascending), dropped bin excluded
+  int32_t* n_items;  // [1]: number of entries of items
+  int32_t* tile_sums;  // [2 * ntiles]: per scan tile, marker sums then non-empty-bin sums
   int ntiles;        // scan tiles over the bins
   unsigned long long* status;  // [4] dropped, nonfinite, refined_fp64, spare
 };
@@ -69,6 +73,7 @@ namespace mls {
 constexpr int kScanTile = 4096;       // bins per scan tile
 constexpr int kScanMaxTiles = 8192;   // bins <= 32 Mi
 constexpr int kBlock = 256;           // threads per block of the per-marker kernels
+constexpr int kSpreadThreads = 128;   // threads per block of the spreading kernel
 
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
@@ -94,6 +99,6 @@ cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s);
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s);
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s);
 size_t spread_smem_bytes(const mls_ctx* ctx);
-cudaError_t spread_configure(const mls_ctx* ctx);
+cudaError_t spread_configure(mls_ctx* ctx);
 
 }  // namespace mls

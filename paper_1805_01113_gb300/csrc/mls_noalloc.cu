@@ -1,7 +1,7 @@
 // mls_build_transfer_noalloc: the build of mls_build_transfer for callers that
 // cannot allocate device memory when they build.  The outputs go to buffers
 // the caller owns; the tile-sort workspace (bin keys and ranks, bin counts,
-// bin offsets, scan tile sums, counters) lives in one file-scope device array
+// bin offsets, the tile list, scan tile sums, counters) lives in one file-scope device array
 // of fixed size instead of a transfer handle.  The kernels are the same ones
 // mls_build_transfer launches.
 #include <mutex>
@@ -21,9 +21,11 @@ constexpr size_t kOffKey = 0;
 constexpr size_t kOffRank = kOffKey + align256(kMaxMarkers * 4);
 constexpr size_t kOffCounts = kOffRank + align256(kMaxMarkers * 4);
 constexpr size_t kOffOffsets = kOffCounts + align256(kMaxBins * 4);
-constexpr size_t kOffTiles = kOffOffsets + align256(kMaxBins * 4);
-constexpr size_t kOffStatus = kOffTiles + align256(kMaxTiles * 4);
-constexpr size_t kScratchBytes = kOffStatus + 256;
+constexpr size_t kOffItems = kOffOffsets + align256(kMaxBins * 4);
+constexpr size_t kOffTiles = kOffItems + align256(kMaxBins * 4);
+constexpr size_t kOffStatus = kOffTiles + align256(2 * kMaxTiles * 4);
+constexpr size_t kOffNItems = kOffStatus + 256;
+constexpr size_t kScratchBytes = kOffNItems + 256;
 static_assert(kScratchBytes == MLS_NOALLOC_SCRATCH_BYTES, "header and layout disagree");
 
 // The workspace.  Every device that loads the library holds it until exit.
@@ -100,6 +102,8 @@ extern "C" int mls_build_transfer_noalloc(mls_ctx* ctx, const void* x, const voi
   T.rank = reinterpret_cast<int32_t*>(s + kOffRank);
   T.counts = reinterpret_cast<int32_t*>(s + kOffCounts);
   T.offsets = reinterpret_cast<int32_t*>(s + kOffOffsets);
+  T.items = reinterpret_cast<int32_t*>(s + kOffItems);
+  T.n_items = reinterpret_cast<int32_t*>(s + kOffNItems);
   T.tile_sums = reinterpret_cast<int32_t*>(s + kOffTiles);
   T.ntiles = (ctx->tiles.nbins + kScanTile - 1) / kScanTile;
   T.status = reinterpret_cast<unsigned long long*>(s + kOffStatus);
