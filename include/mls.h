@@ -55,8 +55,9 @@ extern "C" {
 #define MLS_ERR_OUT_OF_DOMAIN 5  /* mls_transfer_status: some markers were dropped */
 
 /* ---- methods and number types ---------------------------------------- */
-#define MLS_EXACT 0  /* exact-MLS, Eqs. 3-6 */
-#define MLS_FAST  1  /* fast-MLS, Eqs. 9-10 */
+#define MLS_EXACT     0  /* exact-MLS, Eqs. 3-6 */
+#define MLS_FAST      1  /* fast-MLS, Eqs. 9-10 */
+#define MLS_SURROGATE 2  /* learned surrogate of exact-MLS with exact fallback (not in the paper) */
 
 #define MLS_F64  0
 #define MLS_F32  1
@@ -84,6 +85,8 @@ typedef struct {
   int32_t brick_log2[3]; /* spreading tile of 2^b home cells per axis, 1..5 each, default 3 */
   double cond_max;       /* MLS_F32 only: re-solve Eq. 6 in double when cond_1(A) exceeds this; <= 0 disables; default 1e6 */
   int32_t refine;        /* MLS_F32 only: iterative-refinement steps of the 4x4 solve, 0..2, default 1 */
+  double residual_max;   /* MLS_SURROGATE: linear-reproduction residual above which a marker
+                            falls back to exact-MLS, default 1e-4 */
 } mls_options;
 
 /* Device views into a built transfer (borrowed; valid until the next build on
@@ -103,6 +106,7 @@ typedef struct {
   int64_t dropped;       /* markers outside the grid, non-finite, or with a support leaving a walled axis */
   int64_t nonfinite;     /* of which: non-finite position or area */
   int64_t refined_fp64;  /* MLS_F32 exact builds re-solved in double (cond_1(A) > cond_max) */
+  int64_t surrogate_fallback; /* MLS_SURROGATE markers that took the exact-MLS value */
 } mls_status;
 
 typedef struct {
@@ -143,9 +147,10 @@ int mls_marker_prep(mls_ctx* ctx, const void* vertices, int64_t n_vertices,
 
 /* Build the transfer functions of M markers into T (Section 2).
  *   x     device, real[3][M] marker positions; area device, real[M] (A_l, Eq. 7)
- *   method MLS_EXACT (Eqs. 3-6) or MLS_FAST (Eqs. 9-10; the first fast build
+ *   method MLS_EXACT (Eqs. 3-6), MLS_FAST (Eqs. 9-10; the first fast build
  *          on a context tabulates exact shape functions on the sub-Eulerian
- *          mesh, once, on `stream`).
+ *          mesh, once, on `stream`), or MLS_SURROGATE (needs trained or
+ *          loaded parameters, else MLS_ERR_UNSUPPORTED).
  * Markers are sorted into spreading tiles; phi, c, home and perm are written
  * in that order (see mls_transfer_arrays).  Dropped markers get phi = 0,
  * c = 0, home = -1 and are counted in mls_status.
@@ -207,6 +212,61 @@ int mls_fast_table(mls_ctx* ctx, void* stream, const void** table, int64_t* n_cl
 #define MLS_NOALLOC_SCRATCH_BYTES 5293312
 int mls_build_transfer_noalloc(mls_ctx* ctx, const void* x, const void* area, int64_t M, int32_t method,
                                void* phi, void* c, int32_t* home, int32_t* perm, int64_t ld_phi, void* stream);
+
+/* ---- learned surrogate (not in the paper) ------------------------------
+ * On a grid uniform in all but one axis the shape functions of a marker depend
+ * only on its offset t in the home cell and the width ratios along the
+ * non-uniform axis (Section 2, the premise of fast-MLS).  A 6-64-64-27 network
+ * (tanh hidden layers) maps the features
+ *   t_x, t_y, t_z, ln(D_{i-1}/D_i), ln(D_{i+1}/D_i), ln(D_i/D_u)
+ * (D: widths along the non-uniform axis, z when all are uniform; D_u: width of
+ * the first other axis) to the 27 shape functions.  Its output is projected
+ * orthogonally onto {sum phi = 1, sum phi xi = 0} (linear reproduction); a
+ * marker whose residual then exceeds residual_max takes the exact-MLS value.
+ * Parameters are float32, stored flat as W1[64][6], b1[64], W2[64][64],
+ * b2[64], W3[27][64], b3[27] (MLS_MLP_PARAMS values); builds evaluate the
+ * network with bfloat16 operands and float32 accumulation on tensor cores. */
+#define MLS_MLP_PARAMS 6363
+
+typedef struct {
+  int64_t n_samples;     /* training set size, default 1048576 */
+  int32_t epochs;        /* passes over the set, default 128 */
+  int32_t batch;         /* minibatch size, 128..65536 and a multiple of 128, default 1024 */
+  double lr;             /* initial Adam learning rate, default 3e-3 */
+  double lr_final;       /* cosine-decayed final learning rate, default 1e-6 */
+  uint64_t seed;         /* sample, minibatch and initialisation draws, default 1805011135 */
+} mls_train_options;
+
+int mls_train_options_default(mls_train_options* o);
+
+/* Train the context's surrogate on the GPU (synchronous): draw n_samples
+ * training points (offsets and, on a stretched grid, home cells of the
+ * non-uniform axis) with the splitmix64 counter generator, label them with
+ * exact-MLS shape functions computed in double, then run Adam on the mean
+ * squared error with the library's forward/backward kernels.  `loss` (may be
+ * NULL) receives the mean loss of the last epoch.  Allocates its workspace.
+ * MLS_ERR_UNSUPPORTED for more than one non-uniform axis. */
+int mls_surrogate_train(mls_ctx* ctx, const mls_train_options* o, void* stream, double* loss);
+
+/* Copy the flat float32 parameters out of (set = 0) or into (set = 1) the
+ * context; `host` holds MLS_MLP_PARAMS values.  Synchronous. */
+int mls_surrogate_params(mls_ctx* ctx, float* host, int64_t n, int32_t set);
+
+/* Training points first .. first+count-1 of a seed, as mls_surrogate_train
+ * draws them: X device float[count][6], T device float[count][27]. */
+int mls_surrogate_samples(mls_ctx* ctx, int64_t first, int64_t count, uint64_t seed, float* X, float* T,
+                          void* stream);
+
+/* Network on given inputs: X device float[B][6] -> Y device float[B][27].
+ * mode MLS_F32: the float32 training path; MLS_BF16: the bfloat16 tensor-core
+ * path builds use (before projection). */
+int mls_surrogate_forward(mls_ctx* ctx, const float* X, int32_t B, int32_t mode, float* Y, void* stream);
+
+/* Mean squared error over outputs and batch and its gradient for the current
+ * parameters: X device float[B][6], T device float[B][27]; grad device
+ * float[MLS_MLP_PARAMS]; loss device float[1].  B a multiple of 128. */
+int mls_surrogate_loss_grad(mls_ctx* ctx, const float* X, const float* T, int32_t B, float* grad, float* loss,
+                            void* stream);
 
 /* Per-kernel CUDA-event timing on the launching stream (off by default).
  * mls_timing_read synchronises the device, returns up to `max` accumulated

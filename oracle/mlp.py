@@ -190,3 +190,31 @@ def shape_surrogate(grid, x, theta, eps=1.0, residual_max=1e-4, home=None):
         phi[bad] = _mls.shape_exact(grid, x[:, bad], eps, home=sup.home[:, bad]).phi
     phi[~sup.ok] = 0.0
     return _mls.Transfer(phi, sup), bad
+
+
+def training_samples(grid, first, count, seed, eps=1.0):
+    """Training inputs and exact-MLS labels for samples first .. first+count-1.
+
+    Sample s uses counters 4s, 4s+1, 4s+2 for the offsets t_d = u - 1/2 and
+    counter 4s+3 for the home index along the non-uniform axis: with z the
+    draw, lo + floor((z >> 32) * range / 2^32) over the usable cells (1 .. n-2
+    on a walled axis, 0 .. n-1 on a periodic one).  The other axes use their
+    middle cell.  Labels are exact-MLS shape functions (Eqs. 3-6) at the
+    resulting position.  Returns (X (count, 6), phi (count, 27)).
+    """
+    c = class_axis(grid)
+    s = np.arange(first, first + count, dtype=np.uint64)
+    t = np.stack([uniform01(np.uint64(4) * s + np.uint64(q), seed) - 0.5 for q in range(3)])
+    z = splitmix64(np.uint64(4) * s + np.uint64(3), seed)
+    n = grid.n[c]
+    lo, hi = (0, n - 1) if grid.periodic[c] else (1, n - 2)
+    span = np.uint64(hi - lo + 1)
+    cls = lo + (((z >> np.uint64(32)) * span) >> np.uint64(32)).astype(np.int64)
+    home = np.empty((3, count), dtype=np.int64)
+    for d in range(3):
+        home[d] = cls if d == c else grid.n[d] // 2
+    X = features(grid, home, t)
+    x = np.empty((3, count))
+    for d in range(3):
+        x[d] = grid.faces[d][home[d]] + (t[d] + 0.5) * grid.widths[d][home[d]]
+    return X, _mls.shape_exact(grid, x, eps, home=home).phi

@@ -12,7 +12,7 @@ from . import binding as B
 
 DTYPES = {"f64": (B.MLS_F64, torch.float64), "f32": (B.MLS_F32, torch.float32),
           "bf16": (B.MLS_BF16, torch.bfloat16)}
-METHODS = {"exact": B.MLS_EXACT, "fast": B.MLS_FAST}
+METHODS = {"exact": B.MLS_EXACT, "fast": B.MLS_FAST, "surrogate": B.MLS_SURROGATE}
 
 
 def _stream(stream):
@@ -74,7 +74,7 @@ class Context:
     """One grid + option set (mls_create)."""
 
     def __init__(self, faces, periodic, real="f32", field=None, eps=1.0, n_sub=9, brick_log2=(3, 3, 3),
-                 cond_max=1e6, refine=1):
+                 cond_max=1e6, refine=1, residual_max=1e-4):
         self.lib = B.load()
         field = field or real
         self.real_code, self.real_t = DTYPES[real]
@@ -91,7 +91,7 @@ class Context:
         o.real, o.field, o.eps, o.n_sub = self.real_code, self.field_code, float(eps), int(n_sub)
         for d in range(3):
             o.brick_log2[d] = int(brick_log2[d])
-        o.cond_max, o.refine = float(cond_max), int(refine)
+        o.cond_max, o.refine, o.residual_max = float(cond_max), int(refine), float(residual_max)
         self.options = o
         h = C.c_void_p()
         B.check(self.lib.mls_create(C.byref(g), C.byref(o), C.byref(h)), "mls_create")
@@ -157,7 +157,8 @@ class Context:
         rc = self.lib.mls_transfer_status(T.handle, _stream(stream), C.byref(s))
         if rc not in (B.MLS_OK, B.MLS_ERR_OUT_OF_DOMAIN):
             B.check(rc, "mls_transfer_status")
-        return {"code": rc, "dropped": s.dropped, "nonfinite": s.nonfinite, "refined_fp64": s.refined_fp64}
+        return {"code": rc, "dropped": s.dropped, "nonfinite": s.nonfinite, "refined_fp64": s.refined_fp64,
+                "surrogate_fallback": s.surrogate_fallback}
 
     def view(self, T):
         """Zero-copy torch views of the last build: phi (27, M), c (M,), home (M,), perm (M,)."""
@@ -179,6 +180,55 @@ class Context:
         s3 = ns.value ** 3
         dev = torch.device("cuda", torch.cuda.current_device())
         return torch.as_tensor(_DeviceArray(p.value, (nc.value, s3, 27), self.real_t), device=dev)
+
+    # -- learned surrogate ----------------------------------------------------
+    def train_surrogate(self, stream=None, **kw):
+        """Train on the GPU (mls_surrogate_train); keyword options as in mls_train_options."""
+        o = B.mls_train_options()
+        self.lib.mls_train_options_default(C.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        loss = C.c_double()
+        B.check(self.lib.mls_surrogate_train(self.handle, C.byref(o), _stream(stream), C.byref(loss)),
+                "mls_surrogate_train")
+        return loss.value
+
+    def surrogate_params(self, theta=None):
+        """Get (theta None) or set the flat float32 parameters (numpy array of MLS_MLP_PARAMS)."""
+        import numpy as np
+        if theta is None:
+            out = np.empty(B.MLS_MLP_PARAMS, dtype=np.float32)
+            B.check(self.lib.mls_surrogate_params(self.handle, out.ctypes.data_as(C.c_void_p), out.size, 0),
+                    "mls_surrogate_params")
+            return out
+        buf = np.ascontiguousarray(theta, dtype=np.float32)
+        B.check(self.lib.mls_surrogate_params(self.handle, buf.ctypes.data_as(C.c_void_p), buf.size, 1),
+                "mls_surrogate_params")
+        return buf
+
+    def surrogate_samples(self, first, count, seed, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        X = torch.empty((count, 6), dtype=torch.float32, device=dev)
+        T = torch.empty((count, 27), dtype=torch.float32, device=dev)
+        B.check(self.lib.mls_surrogate_samples(self.handle, first, count, seed, _ptr(X), _ptr(T), _stream(stream)),
+                "mls_surrogate_samples")
+        return X, T
+
+    def surrogate_forward(self, X, mode="f32", stream=None):
+        _check_tensor(X, "X", torch.float32)
+        Y = torch.empty((X.shape[0], 27), dtype=torch.float32, device=X.device)
+        B.check(self.lib.mls_surrogate_forward(self.handle, _ptr(X), X.shape[0], DTYPES[mode][0], _ptr(Y),
+                                               _stream(stream)), "mls_surrogate_forward")
+        return Y
+
+    def surrogate_loss_grad(self, X, T, stream=None):
+        _check_tensor(X, "X", torch.float32)
+        _check_tensor(T, "T", torch.float32)
+        g = torch.empty(B.MLS_MLP_PARAMS, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        B.check(self.lib.mls_surrogate_loss_grad(self.handle, _ptr(X), _ptr(T), X.shape[0], _ptr(g), _ptr(loss),
+                                                 _stream(stream)), "mls_surrogate_loss_grad")
+        return float(loss.item()), g
 
     def timing(self, on=True):
         B.check(self.lib.mls_timing_enable(self.handle, 1 if on else 0), "mls_timing_enable")

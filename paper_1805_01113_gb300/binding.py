@@ -18,6 +18,8 @@ MLS_ERR_OUT_OF_DOMAIN = 5
 
 MLS_EXACT = 0
 MLS_FAST = 1
+MLS_SURROGATE = 2
+MLS_MLP_PARAMS = 6363
 
 MLS_F64 = 0
 MLS_F32 = 1
@@ -33,7 +35,8 @@ class mls_grid(C.Structure):
 
 class mls_options(C.Structure):
     _fields_ = [("real", C.c_int32), ("field", C.c_int32), ("eps", C.c_double), ("n_sub", C.c_int32),
-                ("brick_log2", C.c_int32 * 3), ("cond_max", C.c_double), ("refine", C.c_int32)]
+                ("brick_log2", C.c_int32 * 3), ("cond_max", C.c_double), ("refine", C.c_int32),
+                ("residual_max", C.c_double)]
 
 
 class mls_transfer_arrays(C.Structure):
@@ -42,7 +45,13 @@ class mls_transfer_arrays(C.Structure):
 
 
 class mls_status(C.Structure):
-    _fields_ = [("dropped", C.c_int64), ("nonfinite", C.c_int64), ("refined_fp64", C.c_int64)]
+    _fields_ = [("dropped", C.c_int64), ("nonfinite", C.c_int64), ("refined_fp64", C.c_int64),
+                ("surrogate_fallback", C.c_int64)]
+
+
+class mls_train_options(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
+                ("lr_final", C.c_double), ("seed", C.c_uint64)]
 
 
 class mls_kernel_time(C.Structure):
@@ -69,6 +78,14 @@ SIGNATURES = {
     "mls_build_transfer_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                              C.c_void_p]),
+    "mls_train_options_default": (C.c_int, [C.POINTER(mls_train_options)]),
+    "mls_surrogate_train": (C.c_int, [C.c_void_p, C.POINTER(mls_train_options), C.c_void_p, C.POINTER(C.c_double)]),
+    "mls_surrogate_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32]),
+    "mls_surrogate_samples": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
+    "mls_surrogate_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "mls_surrogate_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]),
     "mls_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "mls_timing_read": (C.c_int, [C.c_void_p, C.POINTER(mls_kernel_time), C.c_int32, C.POINTER(C.c_int32)]),
     "mls_strerror": (C.c_char_p, [C.c_int32]),

@@ -109,6 +109,7 @@ int mls_options_default(mls_options* opt) {
   opt->brick_log2[0] = opt->brick_log2[1] = opt->brick_log2[2] = 3;
   opt->cond_max = 1e6;
   opt->refine = 1;
+  opt->residual_max = 1e-4;
   return MLS_OK;
 }
 
@@ -121,6 +122,8 @@ static void free_ctx(mls_ctx* c) {
     cudaFree(c->widths_f[d]);
   }
   cudaFree(c->table);
+  cudaFree(c->mlp_theta);
+  cudaFree(c->mlp_pack);
   for (auto& p : c->events) {
     cudaEventDestroy(p.start);
     cudaEventDestroy(p.stop);
@@ -141,6 +144,7 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
   if (!(opt.eps > 0.0) || !std::isfinite(opt.eps)) return invalid("mls_create: eps must be positive");
   if (opt.n_sub < 3 || opt.n_sub > 33) return invalid("mls_create: n_sub must be in [3, 33]");
   if (opt.refine < 0 || opt.refine > 2) return invalid("mls_create: refine must be 0, 1 or 2");
+  if (!(opt.residual_max > 0.0)) return invalid("mls_create: residual_max must be positive");
   for (int d = 0; d < 3; ++d)
     if (opt.brick_log2[d] < 1 || opt.brick_log2[d] > 5) return invalid("mls_create: brick_log2 must be in [1, 5]");
   int64_t cells = 1;
@@ -209,9 +213,10 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
     return invalid("mls_create: spreading tile too large for shared memory; lower brick_log2");
   }
   cudaError_t e = spread_configure(c);
+  if (e == cudaSuccess) e = mlp_configure();
   if (e != cudaSuccess) {
     free_ctx(c);
-    return cuda_fail(e, "mls_create: spread_configure");
+    return cuda_fail(e, "mls_create: kernel configuration");
   }
   *out = c;
   return MLS_OK;
@@ -336,7 +341,12 @@ int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void*
     set_error("mls_build_transfer: M exceeds the transfer capacity");
     return MLS_ERR_CAPACITY;
   }
-  if (method != MLS_EXACT && method != MLS_FAST) return invalid("mls_build_transfer: unknown method");
+  if (method != MLS_EXACT && method != MLS_FAST && method != MLS_SURROGATE)
+    return invalid("mls_build_transfer: unknown method");
+  if (method == MLS_SURROGATE && (!ctx->mlp_pack || ctx->opt.real != MLS_F32)) {
+    set_error("mls_build_transfer: the surrogate needs a single-precision context with trained or loaded parameters");
+    return MLS_ERR_UNSUPPORTED;
+  }
   if (M > 0 && (!x || !area)) return invalid("mls_build_transfer: NULL marker arrays");
   cudaStream_t s = (cudaStream_t)stream;
   if (method == MLS_FAST) {
@@ -363,8 +373,11 @@ int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void*
   e = launch_scatter(T, M, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: scatter");
-  slot = timer_begin(ctx, method == MLS_EXACT ? "build_exact" : "build_fast", s);
-  e = method == MLS_EXACT ? launch_build_exact(ctx, T, x, area, M, s) : launch_build_fast(ctx, T, x, area, M, s);
+  slot = timer_begin(ctx, method == MLS_EXACT ? "build_exact" : method == MLS_FAST ? "build_fast" : "build_surrogate",
+                     s);
+  e = method == MLS_EXACT  ? launch_build_exact(ctx, T, x, area, M, s)
+      : method == MLS_FAST ? launch_build_fast(ctx, T, x, area, M, s)
+                           : launch_build_surrogate(ctx, T, x, area, M, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: build");
   return MLS_OK;
@@ -415,6 +428,7 @@ int mls_transfer_status(const mls_transfer* T, void* stream, mls_status* out) {
   out->dropped = (int64_t)h[0];
   out->nonfinite = (int64_t)h[1];
   out->refined_fp64 = (int64_t)h[2];
+  out->surrogate_fallback = (int64_t)h[3];
   if (h[0] > 0) {
     set_error("some markers were dropped");
     return MLS_ERR_OUT_OF_DOMAIN;

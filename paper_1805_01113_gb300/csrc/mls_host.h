@@ -41,6 +41,9 @@ struct mls_ctx {
   int class_axis;
   // Persistent grid of the spreading kernel (blocks resident on the device).
   int spread_grid;
+  // Learned surrogate: float32 parameters and the packed bfloat16 copy.
+  float* mlp_theta;
+  unsigned char* mlp_pack;
   // Per-kernel timing.
   int timing;
   std::vector<mls_kernel_timer> timers;
@@ -98,6 +101,26 @@ cudaError_t launch_build_fast(const mls_ctx* ctx, mls_transfer* T, const void* x
 cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s);
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s);
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s);
+// Surrogate (k_mlp.cu).
+void mlp_init_params(uint64_t seed, float* theta);
+int surrogate_class_axis(mls_ctx* ctx);
+cudaError_t mlp_configure();
+size_t mlp_pack_bytes();
+size_t mlp_train_floats(int B);
+cudaError_t launch_mlp_samples(const mls_ctx* ctx, int64_t first, int64_t count, uint64_t seed, float* X, float* T,
+                               cudaStream_t s);
+cudaError_t launch_mlp_grad(const float* theta, const float* X, const float* T, int64_t n_all, int B, bool gather,
+                            uint64_t draw_base, uint64_t seed, float* work, float* grad, float* loss_sum,
+                            cudaStream_t s);
+cudaError_t launch_adam(float* theta, const float* grad, float* m, float* v, float lr, float bc1, float bc2,
+                        cudaStream_t s);
+cudaError_t launch_scale1(float* v, float s, cudaStream_t st);
+cudaError_t launch_mlp_pack(const float* theta, unsigned char* pack, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float* theta, const unsigned char* pack, const float* X, int B, int mode,
+                               float* Y, cudaStream_t s);
+cudaError_t launch_build_surrogate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                                   cudaStream_t s);
+
 size_t spread_smem_bytes(const mls_ctx* ctx);
 cudaError_t spread_configure(mls_ctx* ctx);
 
