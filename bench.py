@@ -43,6 +43,7 @@ def algorithmic_bytes(kernel, rs, u_cells, verts_per_marker):
         "scatter": 12,
         "build_exact": 4 + 4 * rs + 27 * rs + rs + 4,
         "build_fast": 4 + 4 * rs + 27 * rs + rs + 4,
+        "build_surrogate": 4 + 4 * rs + 27 * rs + rs + 4,
         "interp": 27 * rs + 8 + 3 * rs * u_cells + 3 * rs,
         "spread": 27 * rs + rs + 8 + 3 * rs + 6 * rs * u_cells,
     }.get(kernel)
@@ -61,6 +62,9 @@ def parse():
     p.add_argument("--sample-bodies", type=int, default=160, help="bodies in the CPU oracle sample")
     p.add_argument("--grid", type=int, default=None, help="cells per axis (smaller profiling cases)")
     p.add_argument("--bodies", type=int, default=None, help="number of bodies (smaller profiling cases)")
+    p.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-surrogate", action="store_true")
     return p.parse_args()
 
 
@@ -106,28 +110,37 @@ for rep in range(args["reps"]):
     c = oracle.forcing_scale(tr, area)
     ix, iy, iz = tr.sup.idx
     usup = field_at_cells_np(w.modes, w.faces, ix.ravel(), iy.ravel(), iz.ravel()).reshape((3,) + ix.shape)
-    if real == "f32":
-        usup = usup.astype(np.float32).astype(np.float64)
     U = np.einsum("mk,cmk->cm", tr.phi, usup)
     sp = oracle.spread(tr, c, F, g.n)
     times.append(time.perf_counter() - t0)
-keep = slice(0, min(2000, f1 - f0))
-np.savez(args["out"], phi=tr.phi[keep], U=U[:, keep], c=c[keep])
+out = {"phi": tr.phi, "U": U, "c": c, "fk": sp.keys, "fv": sp.values}
+if args.get("fast_too") and args["method"] == "exact":
+    out["phi_fast"] = oracle.shape_fast(g, x, 1.0, 9).phi
+np.savez(args["out"], **out)
 print(json.dumps({"markers": int(f1 - f0), "times": times}))
 """
 
 
-def run_oracle_sample(name, method, bodies, reps, out, kw=None):
+def run_oracle_sample(name, method, bodies, reps, out, kw=None, fast_too=False):
     env = dict(os.environ)
     env["MLS_ROOT"] = ROOT
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     args = json.dumps({"workload": name, "method": method, "bodies": bodies, "reps": reps, "out": out,
-                       "kw": kw or {}})
+                       "kw": kw or {}, "fast_too": fast_too})
     r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, args], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _errs(got, ref):
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = max(float(np.max(np.abs(ref))), 1e-300)
+    return {"max_rel": float(np.max(np.abs(got - ref)) / scale),
+            "rms_rel": float(np.sqrt(np.mean((got - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)))}
 
 
 # ---------------------------------------------------------------- clocks
@@ -214,7 +227,7 @@ def run_ours(a, rank, world, local):
     import torch.distributed as dist
     from paper_1805_01113_gb300 import build_ext
     build_ext.build()
-    from paper_1805_01113_gb300 import api
+    from paper_1805_01113_gb300 import api, autotune
     from workloads.fields import field_full_torch
 
     torch.cuda.set_device(local)
@@ -222,11 +235,11 @@ def run_ours(a, rank, world, local):
     w = workload(a.workload, a.grid, a.bodies)
     real = w.real
     tdt = torch.float32 if real == "f32" else torch.float64
+    ndt = np.float32 if real == "f32" else np.float64
     rs = 4 if real == "f32" else 8
     M = w.n_markers
-    ctx = api.Context(w.faces, w.periodic, real=real)
-    V_host = torch.as_tensor(w.vertices.astype(np.float32 if real == "f32" else np.float64)).pin_memory()
-    F_host = torch.as_tensor(w.forces().astype(np.float32 if real == "f32" else np.float64)).pin_memory()
+    V_host = torch.as_tensor(w.vertices.astype(ndt)).pin_memory()
+    F_host = torch.as_tensor(w.forces().astype(ndt)).pin_memory()
     V = V_host.to(dev)
     tri = torch.as_tensor(w.tri, device=dev)
     F = F_host.to(dev)
@@ -235,9 +248,25 @@ def run_ours(a, rank, world, local):
     x = torch.empty((3, M), dtype=tdt, device=dev)
     area = torch.empty((M,), dtype=tdt, device=dev)
     U = torch.empty((3, M), dtype=tdt, device=dev)
-    T = ctx.transfer(M)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+
+    # Spreading tile shape: autotuned on this workload (exact-MLS step), else 8x8x8.
+    tiles, tune_ms = (3, 3, 3), None
+    api.Context(w.faces, w.periodic, real=real).marker_prep(V, tri, x, area)
+    if not a.no_autotune:
+        tiles, tune_ms = autotune.tune(w.faces, w.periodic, x, area, u, F, "exact", real)
+    ctx = api.Context(w.faces, w.periodic, real=real, brick_log2=tiles)
+    T = ctx.transfer(M)
+    ctx.fast_table()
+    methods = ["exact", "fast"]
+    train = None
+    if real == "f32" and not a.no_surrogate:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = ctx.train_surrogate()
+        train = {"seconds": time.perf_counter() - t0, "final_loss": loss}
+        methods.append("surrogate")
 
     def step(method):
         ctx.marker_prep(V, tri, x, area)
@@ -255,13 +284,29 @@ def run_ours(a, rank, world, local):
     touched = int(torch.count_nonzero(f[0]).item())
     u_cells = touched / M
 
+    graphs = {}
+
+    def run_step(method):
+        if a.graph:
+            if method not in graphs:
+                for _ in range(2):
+                    step(method)
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    step(method)
+                graphs[method] = g
+            graphs[method].replay()
+        else:
+            step(method)
+
     def timed(method, steps, warmup, per_kernel, min_warm_s=0.0):
         # At least `warmup` untimed steps, and at least min_warm_s of load so the
         # clock sampler sees the GPU busy around the timed region.
         t0 = time.perf_counter()
         done = 0
         while done < warmup or time.perf_counter() - t0 < min_warm_s:
-            step(method)
+            run_step(method) if not per_kernel else step(method)
             done += 1
             if done % 16 == 0:
                 torch.cuda.synchronize()
@@ -276,7 +321,7 @@ def run_ours(a, rank, world, local):
         for e0, e1 in evs:
             flush.fill_(1.0)
             e0.record(stream)
-            step(method)
+            step(method) if per_kernel else run_step(method)
             e1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -315,9 +360,20 @@ def run_ours(a, rank, world, local):
                    "gbs": (round(byts[k] * M / (per_launch[k] / 1e3) / 1e9, 1) if byts.get(k) else None)}
                for k in per_launch}
 
-    # the other method, same workload (reported, not the headline)
-    other = "fast" if a.method == "exact" else "exact"
-    ms_o, _ = timed(other, max(3, a.steps // 2), 3, False)
+    # the other methods, same workload (reported, not the headline)
+    others = {}
+    for mth in methods:
+        if mth == a.method:
+            continue
+        ms_o, _ = timed(mth, max(3, a.steps // 2), 3, False)
+        _, kt_o = timed(mth, 3, 1, True)
+        bname = "build_" + mth
+        others[mth] = {"value": M * world / (statistics.mean(ms_o) / 1e3), "ms_per_step": statistics.mean(ms_o),
+                       "build_ms": (kt_o[bname][1] / kt_o[bname][0]) if bname in kt_o else None}
+    if "surrogate" in others:
+        step("surrogate")
+        others["surrogate"]["fallback_rate"] = ctx.status(T)["surrogate_fallback"] / M
+        others["surrogate"]["training"] = train
 
     # end to end through the public API with host buffers: H2D of the step's
     # vertices and forces from pinned memory, D2H of the marker velocities
@@ -347,34 +403,82 @@ def run_ours(a, rank, world, local):
                "d2h_bytes_per_step": U_host.numel() * U_host.element_size(),
                "ms_per_step": 1e3 * statistics.mean(te)}
 
-    # CPU oracle on a bounded sample (rank 0, N = 1 only), plus its error check
-    cpu = None
+    # CPU oracle on a bounded sample (rank 0, N = 1 only): its timing, and the
+    # error of every method and precision mode against it on that sample.
+    cpu, precision = None, None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         nb = min(a.sample_bodies, len(w.body_faces) - 1)
+        ks = int(w.body_faces[nb])
+        xs, as_, Fs = x[:, :ks].contiguous(), area[:ks].contiguous(), F[:, :ks].contiguous()
         with tempfile.TemporaryDirectory() as td:
             out = os.path.join(td, "s.npz")
             kw = {k: v for k, v in (("n", a.grid), ("n_bodies", a.bodies)) if v is not None}
-            r = run_oracle_sample(a.workload, a.method, [0, nb], 1, out, kw)
-            ref = np.load(out)
-            k = ref["phi"].shape[0]
-            v = ctx.view(T)
-            inv = torch.empty(M, dtype=torch.long, device=dev)
-            inv[v["perm"].long()] = torch.arange(M, device=dev)
-            ctx.marker_prep(V, tri, x, area)
-            ctx.build_transfer(T, x, area, a.method)
-            ctx.interpolate(T, u, U)
-            v = ctx.view(T)
-            inv[v["perm"].long()] = torch.arange(M, device=dev)
-            phi_g = v["phi"][:, inv[:k]].double().cpu().numpy().T
-            U_g = U[:, :k].double().cpu().numpy()
-            err = {"phi_max_rel": float(np.max(np.abs(phi_g - ref["phi"])) / np.max(np.abs(ref["phi"]))),
-                   "U_max_rel": float(np.max(np.abs(U_g - ref["U"])) / np.max(np.abs(ref["U"]))),
-                   "U_rms_rel": float(np.sqrt(np.mean((U_g - ref["U"]) ** 2)) / np.sqrt(np.mean(ref["U"] ** 2))),
-                   "markers_compared": int(k)}
+            r = run_oracle_sample(a.workload, "exact", [0, nb], 1, out, kw, fast_too=True)
+            ref = dict(np.load(out))
+        fk = torch.as_tensor(ref["fk"], device=dev)
+
+        def sample_outputs(c, method, field_t):
+            Ts = c.transfer(ks)
+            c.build_transfer(Ts, xs, as_, method)
+            uu = u.to(field_t)
+            Us = c.interpolate(Ts, uu)
+            fs = torch.zeros_like(uu)
+            c.spread(Ts, Fs, fs)
+            v = c.view(Ts)
+            inv = torch.empty(ks, dtype=torch.long, device=dev)
+            inv[v["perm"].long()] = torch.arange(ks, device=dev)
+            phi = v["phi"][:, inv].double().cpu().numpy().T
+            fv = fs.reshape(3, -1)[:, fk].double().cpu().numpy()
+            nf = int(torch.count_nonzero(fs.reshape(3, -1)).item())
+            out = {"phi": phi, "U": Us.double().cpu().numpy(), "f": fv, "f_nonzero_outside": nf - int(
+                np.count_nonzero(fv))}
+            Ts.close()
+            return out
+
+        errs = {}
+        for mth in methods:
+            o = sample_outputs(ctx, mth, tdt)
+            errs[mth] = {"phi_vs_exact": _errs(o["phi"], ref["phi"]), "U": _errs(o["U"], ref["U"]),
+                         "f": _errs(o["f"], ref["fv"])}
+            if mth == "fast":
+                errs[mth]["phi_vs_oracle_fast"] = _errs(o["phi"], ref["phi_fast"])
         cpu = {"value": r["markers"] / min(r["times"]), "unit": "markers/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {nb} bodies ({r['markers']} markers) of the same workload, prep+{a.method} build"
+               "sample": f"first {nb} bodies ({r['markers']} markers) of the same workload, prep+exact build"
                          f"+interp+spread, numpy float64, single thread",
-               "err_vs_fp64_oracle": err}
+               "err_vs_fp64_oracle": errs}
+        if real == "f32":
+            precision = {}
+            cb = api.Context(w.faces, w.periodic, real="f32", field="bf16", brick_log2=tiles)
+            ub, fb = u.to(torch.bfloat16), torch.zeros(u.shape, dtype=torch.bfloat16, device=dev)
+            Tb = cb.transfer(M)
+
+            def step_b():
+                cb.marker_prep(V, tri, x, area)
+                cb.build_transfer(Tb, x, area, "exact")
+                cb.interpolate(Tb, ub, U)
+                cb.spread(Tb, F, fb)
+
+            for _ in range(3):
+                step_b()
+            torch.cuda.synchronize()
+            tb = []
+            for _ in range(max(3, a.steps // 2)):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                step_b()
+                e1.record()
+                torch.cuda.synchronize()
+                tb.append(e0.elapsed_time(e1))
+            ob = sample_outputs(cb, "exact", torch.bfloat16)
+            precision["bf16_fields"] = {"value": M / (statistics.mean(tb) / 1e3),
+                                        "U": _errs(ob["U"], ref["U"]), "f": _errs(ob["f"], ref["fv"]),
+                                        "bound_stated": 1e-2}
+            c0 = api.Context(w.faces, w.periodic, real="f32", refine=0, brick_log2=tiles)
+            o0 = sample_outputs(c0, "exact", torch.float32)
+            precision["f32_solve_no_refinement"] = {"phi": _errs(o0["phi"], ref["phi"])}
+            precision["f32_solve_one_refinement"] = {"phi": errs["exact"]["phi_vs_exact"],
+                                                     "fp64_fallbacks": ctx.status(T)["refined_fp64"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "markers/s", "n_gpus": world, "steps": a.steps,
@@ -382,13 +486,14 @@ def run_ours(a, rank, world, local):
         "vs_baseline": None, "dtype": real, "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[a.workload] if a.grid is None and a.bodies is None else
                    f"{a.workload} variant: {len(w.body_faces) - 1} bodies, {w.n[0]}x{w.n[1]}x{w.n[2]} grid",
-                   "markers_per_gpu": M, "method": a.method,
-                   "grid": list(w.n), "l2": "flushed by a 256 MiB write before every timed step",
+                   "markers_per_gpu": M, "method": a.method, "grid": list(w.n),
+                   "l2": "flushed by a 256 MiB write before every timed step",
                    "step": "marker_prep + build_transfer + interpolate + spread",
+                   "graph": bool(a.graph), "tiles_log2": list(tiles),
+                   "autotune_ms": {str(k): round(v, 4) for k, v in tune_ms.items()} if tune_ms else None,
                    "touched_cells_per_marker": round(u_cells, 4)},
-        "roofline": roof, "kernels": kernels, "gpu_launches": launches,
-        other: {"value": M * world / (statistics.mean(ms_o) / 1e3), "ms_per_step": statistics.mean(ms_o)},
-        "e2e": e2e, "clocks": clocks, "cpu_baseline": cpu,
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches, "methods": others,
+        "precision": precision, "e2e": e2e, "clocks": clocks, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -398,14 +503,15 @@ def run_ours(a, rank, world, local):
 def run_reference(a, rank, world):
     if rank != 0:
         return
-    w = workload(a.workload)
+    w = workload(a.workload, a.grid, a.bodies)
     nb = 20
     times = []
     steps = max(1, a.steps)
     for s in range(a.warmup + steps):
         b0 = (s * nb) % (len(w.body_faces) - 1 - nb)
         with tempfile.TemporaryDirectory() as td:
-            r = run_oracle_sample(a.workload, a.method, [b0, b0 + nb], 1, os.path.join(td, "s.npz"))
+            kw = {k: v for k, v in (("n", a.grid), ("n_bodies", a.bodies)) if v is not None}
+            r = run_oracle_sample(a.workload, a.method, [b0, b0 + nb], 1, os.path.join(td, "s.npz"), kw)
         if s >= a.warmup:
             times.append(r["times"][0] / r["markers"])
     per_marker = statistics.mean(times)
