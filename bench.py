@@ -195,14 +195,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on this
+    workload (default sizes), if the kernel's source is unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(p))
     except Exception:
         return None
-    ent = data.get(kernel)
+    ent = data.get(kernel, {}).get(workload)
     if not ent:
         return None
     src = os.path.join(ROOT, "paper_1805_01113_gb300", "csrc", ent["source"])
@@ -355,7 +356,7 @@ def run_ours(a, rank, world, local):
     roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": (ach / pk["hbm_gbs"]) if ach else None, "peak_source": pk_src,
             "algorithmic_bytes_per_launch": byts[dom] * M if byts.get(dom) else None,
-            "traffic": traffic_for(dom)}
+            "traffic": traffic_for(dom, a.workload) if a.grid is None and a.bodies is None else None}
     kernels = {k: {"ms_per_launch": round(per_launch[k], 5), "launches_per_step": kt[k][0] / a.steps,
                    "gbs": (round(byts[k] * M / (per_launch[k] / 1e3) / 1e9, 1) if byts.get(k) else None)}
                for k in per_launch}
