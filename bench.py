@@ -75,6 +75,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world, device):
+    """The largest `value` over all ranks (every rank gets it); identity for one rank."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(markers_per_rank, world, steps, slowest_ms):
+    """Whole-job markers/s: the markers all ranks processed over the slowest rank's time."""
+    return world * markers_per_rank * steps / (slowest_ms / 1e3)
+
+
 def workload(name, grid=None, bodies=None):
     from workloads import make_workload
     kw = {}
@@ -337,12 +353,8 @@ def run_ours(a, rank, world, local):
     clk.start()
     ms, _ = timed(a.method, a.steps, a.warmup, False, min_warm_s=1.5)
     clocks = clk.stop()
-    total_ms = sum(ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * M * a.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(ms), world, dev)
+    value = job_throughput(M, world, a.steps, total_ms)
 
     # per-kernel pass (events around each kernel on the launching stream)
     ms_k, kt = timed(a.method, a.steps, 2, True)
@@ -505,11 +517,12 @@ def run_reference(a, rank, world):
     if rank != 0:
         return
     w = workload(a.workload, a.grid, a.bodies)
-    nb = 20
+    n_bodies = len(w.body_faces) - 1
+    nb = min(20, n_bodies)
     times = []
     steps = max(1, a.steps)
     for s in range(a.warmup + steps):
-        b0 = (s * nb) % (len(w.body_faces) - 1 - nb)
+        b0 = (s * nb) % (n_bodies - nb) if n_bodies > nb else 0
         with tempfile.TemporaryDirectory() as td:
             kw = {k: v for k, v in (("n", a.grid), ("n_bodies", a.bodies)) if v is not None}
             r = run_oracle_sample(a.workload, a.method, [b0, b0 + nb], 1, os.path.join(td, "s.npz"), kw)
