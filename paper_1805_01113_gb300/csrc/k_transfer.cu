@@ -84,27 +84,52 @@ template <> __device__ __forceinline__ void add_field<float, __nv_bfloat16>(__nv
   atomicAdd(p, __float2bfloat16_rn(v));
 }
 
-// Shared-memory layout of one spreading block (bytes), shared by host and device.
+// Accumulator geometry of a spreading tile (tile plus one-cell halo): rows
+// of AX cells (x padded to 4-aligned field groups with VEC), AY rows per
+// plane, AZ planes.  Planes are padded by 4 cells so that cells of one
+// column in different planes fall in different shared-memory banks (with a
+// plane of a multiple of 32 cells every plane would alias the same banks).
+struct AccShape {
+  int AX, AY, AZ, PS, ACC, XOFF;
+  __host__ __device__ AccShape(int lx, int ly, int lz, bool vec) {
+    XOFF = vec ? 4 : 1;
+    AX = (1 << lx) + 2 * XOFF;
+    AY = (1 << ly) + 2;
+    AZ = (1 << lz) + 2;
+    PS = AY * AX + 4;
+    ACC = AZ * PS;
+  }
+};
+
+// Shared-memory bytes of one spreading block: the accumulator (3 components)
+// and the 27 node offsets.
 struct SpreadSmem {
-  int acc, offs, total;
+  int offs, total;
   __host__ __device__ SpreadSmem(int rs, int lx, int ly, int lz, bool vec) {
-    const int xoff = vec ? 4 : 1;
-    const int ACC = ((1 << lx) + 2 * xoff) * ((1 << ly) + 2) * ((1 << lz) + 2);
-    acc = 0;
-    offs = acc + 3 * ACC * rs;                     // 27 node offsets inside the accumulator
+    const AccShape A(lx, ly, lz, vec);
+    offs = 3 * A.ACC * rs;
     total = (offs + 27 * 4 + 15) & ~15;
   }
 };
 
-__device__ __forceinline__ float block_max(float v, float* red) {
+__device__ __forceinline__ void block_max3(float v[3], float* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] = fmaxf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[3 * w] = v[0];
+    red[3 * w + 1] = v[1];
+    red[3 * w + 2] = v[2];
+  }
   __syncthreads();
-  float m = red[0];
 #pragma unroll
-  for (int w = 1; w < kSpreadThreads / 32; ++w) m = fmaxf(m, red[w]);
-  return m;
+  for (int q = 0; q < 3; ++q) {
+    float m = red[q];
+    for (int ww = 1; ww < kSpreadThreads / 32; ++ww) m = fmaxf(m, red[3 * ww + q]);
+    v[q] = m;
+  }
 }
 
 // round-to-nearest integer of x for |x| <= 2^22: adding 1.5 * 2^23 leaves the
@@ -114,16 +139,17 @@ __device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 
 // f_k += sum_l c_l phi_k^l F_l (text after Eq. 7), single precision.
 // Persistent blocks walk the list of non-empty spreading tiles, taking up to
 // 128 markers of a tile at a time (one per thread).  For such a chunk a block
-// finds the largest |c_l F_l|, scales contributions by a power of two so that
-// any |phi| <= 1 term is at most 2^22 units, rounds them to integers and adds
-// them into a shared-memory accumulator (tile plus one-cell halo) with native
+// finds, per component, the largest |c_l F_l| and scales contributions by a
+// power of two so that any |phi| <= 1/2 term is at most 2^22 units, rounds
+// them to integers and adds them into a shared-memory accumulator with native
 // 32-bit integer atomics; a cell's sum stays below 128 * 2^22 = 2^29.  A term
-// outside that range (|phi| > 1) is added to f directly with a float atomic.
-// Each non-zero cell is then converted back and added to f with one global
-// atomic per component.  The quantum is 2^-21 of the chunk's largest |c F|.
-// With VEC the accumulator rows are padded to 4-aligned x groups of the field
-// ([ox-4, ox+2^l+4)) and flushed with 16-byte vector atomics (zero lanes of a
-// group add nothing).  A chunk with non-finite forces is added directly.
+// outside that range (|phi| > 1/2, rare for MLS) is added to f directly with
+// a float atomic.  Each non-zero cell is then converted back and added to f
+// with one global atomic per component; the quantum is at most 2^-22 of the
+// chunk's largest |c F| for that component.  With VEC the accumulator rows are
+// padded to 4-aligned x groups of the field ([ox-4, ox+2^l+4)) and flushed
+// with 16-byte vector atomics (zero lanes of a group add nothing).  A chunk
+// with non-finite forces is added directly.
 template <typename FT, bool VEC>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, const float* __restrict__ phi,
                                                            const float* __restrict__ cl,
@@ -135,17 +161,17 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
                                                            const int32_t* __restrict__ counts, int64_t M, int64_t cap,
                                                            const float* __restrict__ F, FT* __restrict__ f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const AccShape A(tl.l[0], tl.l[1], tl.l[2], VEC);
   const SpreadSmem L(4, tl.l[0], tl.l[1], tl.l[2], VEC);
-  int* acc = reinterpret_cast<int*>(smem_raw + L.acc);
+  int* acc = reinterpret_cast<int*>(smem_raw);
   int* s_off = reinterpret_cast<int*>(smem_raw + L.offs);
-  __shared__ float s_red[kSpreadThreads / 32];
+  __shared__ float s_red[3 * (kSpreadThreads / 32)];
   constexpr int XOFF = VEC ? 4 : 1;
-  const int AX = (1 << tl.l[0]) + 2 * XOFF, AY = (1 << tl.l[1]) + 2, AZ = (1 << tl.l[2]) + 2;
-  const int ACC = AX * AY * AZ;
+  const int AX = A.AX, AY = A.AY, AZ = A.AZ, PS = A.PS, ACC = A.ACC;
   const int tid = threadIdx.x;
   const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
   const int n_items = *n_items_p;
-  if (tid < 27) s_off[tid] = ((tid / 9) * AY + (tid / 3) % 3) * AX + tid % 3;
+  if (tid < 27) s_off[tid] = (tid / 9) * PS + ((tid / 3) % 3) * AX + tid % 3;
 
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int b = items[it];
@@ -156,25 +182,26 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
       const int64_t j = j0 + tid;
       const bool act = j < start + cnt;
       int i[3] = {0, 0, 0};
-      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      float v[3] = {0.f, 0.f, 0.f};
       if (act) {
         decode_home(home[j], D, i);
         const int64_t m = perm[j];
         const float c = cl[j];
-        v0 = c * F[m];
-        v1 = c * F[M + m];
-        v2 = c * F[2 * M + m];
+        v[0] = c * F[m];
+        v[1] = c * F[M + m];
+        v[2] = c * F[2 * M + m];
       }
       for (int e = tid; e < 3 * ACC / 4; e += kSpreadThreads)
         reinterpret_cast<int4*>(acc)[e] = make_int4(0, 0, 0, 0);
-      const float vmax = block_max(fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2))), s_red);  // barrier inside
+      float vm[3] = {fabsf(v[0]), fabsf(v[1]), fabsf(v[2])};
+      block_max3(vm, s_red);                         // barrier inside: zeroing and s_off are complete
+      const float vmax = fmaxf(vm[0], fmaxf(vm[1], vm[2]));
       if (vmax == 0.f) {
         __syncthreads();
         continue;
       }
       if (!isfinite(vmax)) {
         if (act) {
-          const float v[3] = {v0, v1, v2};
           for (int k = 0; k < 27; ++k) {
             const int gx = wrap(i[0] + k % 3 - 1, D.n[0], D.periodic[0]);
             const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);
@@ -187,20 +214,25 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
         __syncthreads();
         continue;
       }
-      int ex;
-      frexpf(vmax, &ex);                             // vmax < 2^ex
-      const float scale = ldexpf(1.f, 22 - ex);      // |p v| * scale <= 2^22 for |p| <= 1
-      const float inv_scale = ldexpf(1.f, ex - 22);
+      // Per component: vm < 2^ex, scale 2^(23 - ex) keeps |p v| * scale <= 2^22 for |p| <= 1/2.
+      float scale[3], inv_scale[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        int ex;
+        frexpf(vm[q] > 0.f ? vm[q] : vmax, &ex);
+        scale[q] = ldexpf(1.f, 23 - ex);
+        inv_scale[q] = ldexpf(1.f, ex - 23);
+      }
       if (act) {
-        const float s0 = v0 * scale, s1 = v1 * scale, s2 = v2 * scale;
-        const int base = ((i[2] - oz) * AY + (i[1] - oy)) * AX + (i[0] - ox) + XOFF - 1;
+        const float q0 = v[0] * scale[0], q1 = v[1] * scale[1], q2 = v[2] * scale[2];
+        const int base = (i[2] - oz) * PS + (i[1] - oy) * AX + (i[0] - ox) + XOFF - 1;
         float p[27];
 #pragma unroll
         for (int k = 0; k < 27; ++k) p[k] = phi[k * cap + j];
 #pragma unroll
         for (int k = 0; k < 27; ++k) {
           const int li = base + s_off[k];
-          const float x0 = p[k] * s0, x1 = p[k] * s1, x2 = p[k] * s2;
+          const float x0 = p[k] * q0, x1 = p[k] * q1, x2 = p[k] * q2;
           if (fmaxf(fabsf(x0), fmaxf(fabsf(x1), fabsf(x2))) <= 4194304.0f) {
             atomicAdd(&acc[li], round_small(x0));
             atomicAdd(&acc[ACC + li], round_small(x1));
@@ -210,9 +242,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
             const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);
             const int gz = wrap(i[2] + k / 9 - 1, D.n[2], D.periodic[2]);
             const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
-            add_field<float, FT>(f + o, p[k] * v0);
-            add_field<float, FT>(f + N + o, p[k] * v1);
-            add_field<float, FT>(f + 2 * N + o, p[k] * v2);
+            add_field<float, FT>(f + o, p[k] * v[0]);
+            add_field<float, FT>(f + N + o, p[k] * v[1]);
+            add_field<float, FT>(f + 2 * N + o, p[k] * v[2]);
           }
         }
       }
@@ -222,7 +254,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
         for (int g = tid; g < G * AY * AZ; g += kSpreadThreads) {
           const int q = g % G, row = g / G;
           const int ey = row % AY, ez = row / AY;
-          const int e = row * AX + 4 * q;
+          const int e = ez * PS + ey * AX + 4 * q;
           const int4 a0 = *reinterpret_cast<const int4*>(&acc[e]);
           const int4 a1 = *reinterpret_cast<const int4*>(&acc[ACC + e]);
           const int4 a2 = *reinterpret_cast<const int4*>(&acc[2 * ACC + e]);
@@ -234,30 +266,30 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
           if (gx < 0 || gx >= D.n[0]) {
             if (!D.periodic[0]) continue;
             gx = gx < 0 ? gx + D.n[0] : gx - D.n[0];
-            if (gx < 0 || gx >= D.n[0]) continue;      // padding beyond one period holds no sums
+            if (gx < 0 || gx >= D.n[0]) continue;        // padding beyond one period holds no sums
           }
           const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
           const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
           float* fo = reinterpret_cast<float*>(f) + ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
-          if (n0)
-            red_add_v4(fo, a0.x * inv_scale, a0.y * inv_scale, a0.z * inv_scale, a0.w * inv_scale);
-          if (n1)
-            red_add_v4(fo + N, a1.x * inv_scale, a1.y * inv_scale, a1.z * inv_scale, a1.w * inv_scale);
-          if (n2)
-            red_add_v4(fo + 2 * N, a2.x * inv_scale, a2.y * inv_scale, a2.z * inv_scale, a2.w * inv_scale);
+          const float u0 = inv_scale[0], u1 = inv_scale[1], u2 = inv_scale[2];
+          if (n0) red_add_v4(fo, a0.x * u0, a0.y * u0, a0.z * u0, a0.w * u0);
+          if (n1) red_add_v4(fo + N, a1.x * u1, a1.y * u1, a1.z * u1, a1.w * u1);
+          if (n2) red_add_v4(fo + 2 * N, a2.x * u2, a2.y * u2, a2.z * u2, a2.w * u2);
         }
       } else {
         for (int e = tid; e < ACC; e += kSpreadThreads) {
+          const int ez = e / PS, r = e - ez * PS;
+          if (r >= AY * AX) continue;                    // plane padding
           const int a0 = acc[e], a1 = acc[ACC + e], a2 = acc[2 * ACC + e];
           if ((a0 | a1 | a2) != 0) {
-            const int ex2 = e % AX, ey = (e / AX) % AY, ez = e / (AX * AY);
+            const int ey = r / AX, ex2 = r - ey * AX;
             const int gx = wrap(ox - XOFF + ex2, D.n[0], D.periodic[0]);
             const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
             const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
             const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
-            if (a0) add_field<float, FT>(f + o, a0 * inv_scale);
-            if (a1) add_field<float, FT>(f + N + o, a1 * inv_scale);
-            if (a2) add_field<float, FT>(f + 2 * N + o, a2 * inv_scale);
+            if (a0) add_field<float, FT>(f + o, a0 * inv_scale[0]);
+            if (a1) add_field<float, FT>(f + N + o, a1 * inv_scale[1]);
+            if (a2) add_field<float, FT>(f + 2 * N + o, a2 * inv_scale[2]);
           }
         }
       }
@@ -343,8 +375,9 @@ static bool spread_vec(const mls_ctx* ctx) {
 }
 
 size_t spread_smem_bytes(const mls_ctx* ctx) {
-  const int rs = ctx->opt.real == MLS_F64 ? 8 : 4;
-  return (size_t)SpreadSmem(rs, ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2], spread_vec(ctx)).total;
+  if (ctx->opt.real == MLS_F64)
+    return (size_t)SpreadSmem(8, ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2], false).total;
+  return (size_t)SpreadSmem(4, ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2], spread_vec(ctx)).total;
 }
 
 template <typename K>
@@ -358,6 +391,7 @@ static cudaError_t configure_kernel(mls_ctx* ctx, K kernel, int smem) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSpreadThreads, smem);
   if (e != cudaSuccess) return e;
   ctx->spread_grid = (per_sm > 0 ? per_sm : 1) * sms;
+  ctx->spread_threads = kSpreadThreads;
   return cudaSuccess;
 }
 
@@ -392,7 +426,7 @@ cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void*
 
 template <typename FT, bool VEC>
 static void launch_spread_one(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s) {
-  k_spread<FT, VEC><<<ctx->spread_grid, kSpreadThreads, spread_smem_bytes(ctx), s>>>(
+  k_spread<FT, VEC><<<ctx->spread_grid, ctx->spread_threads, spread_smem_bytes(ctx), s>>>(
       dims_of(ctx), ctx->tiles, (const float*)T->phi, (const float*)T->c, T->home, T->perm, T->items, T->n_items,
       T->offsets, T->counts, T->M, T->cap, (const float*)F, (FT*)f);
 }

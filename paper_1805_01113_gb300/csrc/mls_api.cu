@@ -208,7 +208,7 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
     return invalid("mls_create: too many spreading tiles; raise brick_log2");
   }
   c->tiles.nbins = (int)nbins;
-  if (spread_smem_bytes(c) > 200 * 1024) {
+  if (spread_smem_bytes(c) > 200 * 1024 + 256) {
     free_ctx(c);
     return invalid("mls_create: spreading tile too large for shared memory; lower brick_log2");
   }

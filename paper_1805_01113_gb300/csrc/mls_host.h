@@ -41,6 +41,7 @@ struct mls_ctx {
   int class_axis;
   // Persistent grid of the spreading kernel (blocks resident on the device).
   int spread_grid;
+  int spread_threads;
   // Learned surrogate: float32 parameters and the packed bfloat16 copy.
   float* mlp_theta;
   unsigned char* mlp_pack;
