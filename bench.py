@@ -35,7 +35,7 @@ WORKLOAD_TEXT = {
 }
 
 # Algorithmic bytes per marker of each kernel (float32 path; u_cells = distinct
-# touched cells per marker, measured).  See DESIGN.md, "Roofline".
+# touched cells per marker, measured): the bytes each kernel must move at least.
 def algorithmic_bytes(kernel, rs, u_cells, verts_per_marker):
     return {
         "marker_prep": 12 + 3 * rs * verts_per_marker + 4 * rs,

@@ -8,7 +8,7 @@ of a marker depend only on its offset t in the home cell and the width ratios
 of the non-uniform axis (Section 2, premise of fast-MLS), so a small network
 can map those to the 27 values.
 
-Readings (also in DESIGN.md):
+Readings:
   * features (6): t_x, t_y, t_z, ln(D_{i-1}/D_i), ln(D_{i+1}/D_i), ln(D_i/D_u)
     with D the widths along the non-uniform axis (z when all are uniform, then
     the three ratio features are 0) and D_u the width of the first other axis;

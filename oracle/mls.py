@@ -12,7 +12,7 @@ spreading f_k = sum_l c_l phi_k^l F_l with c_l from Eq. 8, and fast-MLS
 (Eqs. 9-10: Shepard interpolation of exact shape functions tabulated on a
 sub-Eulerian mesh of the home cell).
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * W is a Gaussian, W = exp(-r^2/eps^2), r measured per axis in units of the
     home cell's width (the paper only says the weight is a free choice).
   * Support nodes are cell centres; the home cell is the cell with
