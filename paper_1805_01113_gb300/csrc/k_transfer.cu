@@ -13,16 +13,35 @@ template <typename R, typename FT> __device__ __forceinline__ R load_field(const
 }
 template <> __device__ __forceinline__ double load_field<double, double>(const double* p) { return __ldg(p); }
 
+// Division by a fixed divisor d >= 1 of numerators n < 2^31 by one 64-bit
+// multiply: with l = ceil(log2 d) and m = floor(2^(32+l) / d) + 1, the error
+// of m / 2^(32+l) against 1/d is below 1 / (d 2^(32+l)) per unit of n, so
+// floor(n m / 2^(32+l)) = floor(n / d) while n < 2^31 <= 2^(32+l) / 2.
+struct FastDiv {
+  unsigned long long m;
+  int shift;
+  int d;
+  void init(int divisor) {
+    d = divisor;
+    int l = 0;
+    while ((1LL << l) < (long long)divisor) ++l;
+    shift = 32 + l;
+    m = (unsigned long long)(((unsigned __int128)1 << shift) / (unsigned)divisor) + 1ULL;
+  }
+  __device__ __forceinline__ int div(int n) const { return (int)(((unsigned long long)(unsigned)n * m) >> shift); }
+};
+
 struct Dims {
   int n[3];
   int periodic[3];
+  FastDiv div0, div1;  // by n[0] and by n[1]
 };
 
 __device__ __forceinline__ void decode_home(int32_t h, const Dims& D, int i[3]) {
-  i[0] = h % D.n[0];
-  const int r = h / D.n[0];
-  i[1] = r % D.n[1];
-  i[2] = r / D.n[1];
+  const int r = D.div0.div(h);
+  i[0] = h - r * D.n[0];
+  i[2] = D.div1.div(r);
+  i[1] = r - i[2] * D.n[1];
 }
 
 // U_l = sum_k phi_k^l u_k for the 3 components (text after Eq. 6).  One
@@ -101,14 +120,16 @@ struct AccShape {
   }
 };
 
-// Shared-memory bytes of one spreading block: the accumulator (3 components)
-// and the 27 node offsets.
+// Shared-memory bytes of one spreading block: the accumulator (3 components),
+// then per accumulator row (y, z) its offset in the accumulator, its global
+// row index and a touched flag.
 struct SpreadSmem {
-  int offs, total;
+  int rows, total;
   __host__ __device__ SpreadSmem(int rs, int lx, int ly, int lz, bool vec) {
     const AccShape A(lx, ly, lz, vec);
-    offs = 3 * A.ACC * rs;
-    total = (offs + 27 * 4 + 15) & ~15;
+    const int R = A.AY * A.AZ;
+    rows = (3 * A.ACC * rs + 15) & ~15;
+    total = (rows + 8 * R + R + 15) & ~15;
   }
 };
 
@@ -142,15 +163,17 @@ __device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 
 // finds, per component, the largest |c_l F_l| and scales contributions by a
 // power of two so that any |phi| <= 1/2 term is at most 2^22 units, rounds
 // them to integers and adds them into a shared-memory accumulator with native
-// 32-bit integer atomics; a cell's sum stays below 128 * 2^22 = 2^29.  A term
-// outside that range (|phi| > 1/2, rare for MLS) is added to f directly with
-// a float atomic.  Each non-zero cell is then converted back and added to f
-// with one global atomic per component; the quantum is at most 2^-22 of the
-// chunk's largest |c F| for that component.  With VEC the accumulator rows are
-// padded to 4-aligned x groups of the field ([ox-4, ox+2^l+4)) and flushed
-// with 16-byte vector atomics (zero lanes of a group add nothing).  A chunk
-// with non-finite forces is added directly.
-template <typename FT, bool VEC>
+// 32-bit integer atomics; a cell's sum stays below 128 * 2^22 = 2^29.  A
+// marker with some |phi| > 1/2 (rare for MLS) adds those terms to f directly
+// with float atomics.  Each marker flags the 9 accumulator rows its support
+// touches; only flagged rows are converted back, added to f with one global
+// atomic per component and cell (per 4 cells with VEC), and reset to zero.
+// The quantum is at most 2^-22 of the chunk's largest |c F| for that
+// component.  With VEC the accumulator rows are padded to 4-aligned x groups
+// of the field ([ox-4, ox+2^l+4)) and flushed with 16-byte vector atomics
+// (zero lanes of a group add nothing).  A chunk with non-finite forces is
+// added directly.
+template <typename FT, bool VEC, int LX>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, const float* __restrict__ phi,
                                                            const float* __restrict__ cl,
                                                            const int32_t* __restrict__ home,
@@ -161,23 +184,32 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
                                                            const int32_t* __restrict__ counts, int64_t M, int64_t cap,
                                                            const float* __restrict__ F, FT* __restrict__ f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const AccShape A(tl.l[0], tl.l[1], tl.l[2], VEC);
-  const SpreadSmem L(4, tl.l[0], tl.l[1], tl.l[2], VEC);
-  int* acc = reinterpret_cast<int*>(smem_raw);
-  int* s_off = reinterpret_cast<int*>(smem_raw + L.offs);
-  __shared__ float s_red[3 * (kSpreadThreads / 32)];
   constexpr int XOFF = VEC ? 4 : 1;
-  const int AX = A.AX, AY = A.AY, AZ = A.AZ, PS = A.PS, ACC = A.ACC;
+  constexpr int AX = (1 << LX) + 2 * XOFF;
+  const AccShape A(LX, tl.l[1], tl.l[2], VEC);
+  const SpreadSmem L(4, LX, tl.l[1], tl.l[2], VEC);
+  const int AY = A.AY, PS = A.PS, ACC = A.ACC, ROWS = AY * A.AZ;
+  int* acc = reinterpret_cast<int*>(smem_raw);
+  int* row_a = reinterpret_cast<int*>(smem_raw + L.rows);
+  int* row_g = row_a + ROWS;
+  unsigned char* flag = reinterpret_cast<unsigned char*>(row_g + ROWS);
+  __shared__ float s_red[3 * (kSpreadThreads / 32)];
   const int tid = threadIdx.x;
   const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
   const int n_items = *n_items_p;
-  if (tid < 27) s_off[tid] = (tid / 9) * PS + ((tid / 3) % 3) * AX + tid % 3;
+  for (int e = tid; e < 3 * ACC; e += kSpreadThreads) acc[e] = 0;
+  for (int r = tid; r < ROWS; r += kSpreadThreads) flag[r] = 0;
 
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int b = items[it];
     const int start = offsets[b], cnt = counts[b];
     const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
-    const int ox = bx << tl.l[0], oy = by << tl.l[1], oz = bz << tl.l[2];
+    const int ox = bx << LX, oy = by << tl.l[1], oz = bz << tl.l[2];
+    for (int r = tid; r < ROWS; r += kSpreadThreads) {
+      const int ey = r % AY, ez = r / AY;
+      row_a[r] = ez * PS + ey * AX;
+      row_g[r] = wrap(oz - 1 + ez, D.n[2], D.periodic[2]) * D.n[1] + wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
+    }
     for (int j0 = start; j0 < start + cnt; j0 += kSpreadThreads) {
       const int64_t j = j0 + tid;
       const bool act = j < start + cnt;
@@ -191,10 +223,8 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
         v[1] = c * F[M + m];
         v[2] = c * F[2 * M + m];
       }
-      for (int e = tid; e < 3 * ACC / 4; e += kSpreadThreads)
-        reinterpret_cast<int4*>(acc)[e] = make_int4(0, 0, 0, 0);
       float vm[3] = {fabsf(v[0]), fabsf(v[1]), fabsf(v[2])};
-      block_max3(vm, s_red);                         // barrier inside: zeroing and s_off are complete
+      block_max3(vm, s_red);                         // barrier inside: row tables and resets are complete
       const float vmax = fmaxf(vm[0], fmaxf(vm[1], vm[2]));
       if (vmax == 0.f) {
         __syncthreads();
@@ -225,75 +255,105 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
       }
       if (act) {
         const float q0 = v[0] * scale[0], q1 = v[1] * scale[1], q2 = v[2] * scale[2];
-        const int base = (i[2] - oz) * PS + (i[1] - oy) * AX + (i[0] - ox) + XOFF - 1;
-        float p[27];
+        const int lx = i[0] - ox, ly = i[1] - oy, lz = i[2] - oz;
+        const int base = lz * PS + ly * AX + lx + XOFF - 1;
+        const int r0 = lz * AY + ly;
 #pragma unroll
-        for (int k = 0; k < 27; ++k) p[k] = phi[k * cap + j];
+        for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+          for (int cy = 0; cy < 3; ++cy) flag[r0 + cz * AY + cy] = 1;
+        float p[27];
+        float pmax = 0.f;
 #pragma unroll
         for (int k = 0; k < 27; ++k) {
-          const int li = base + s_off[k];
-          const float x0 = p[k] * q0, x1 = p[k] * q1, x2 = p[k] * q2;
-          if (fmaxf(fabsf(x0), fmaxf(fabsf(x1), fabsf(x2))) <= 4194304.0f) {
-            atomicAdd(&acc[li], round_small(x0));
-            atomicAdd(&acc[ACC + li], round_small(x1));
-            atomicAdd(&acc[2 * ACC + li], round_small(x2));
-          } else {
-            const int gx = wrap(i[0] + k % 3 - 1, D.n[0], D.periodic[0]);
-            const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);
-            const int gz = wrap(i[2] + k / 9 - 1, D.n[2], D.periodic[2]);
-            const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
-            add_field<float, FT>(f + o, p[k] * v[0]);
-            add_field<float, FT>(f + N + o, p[k] * v[1]);
-            add_field<float, FT>(f + 2 * N + o, p[k] * v[2]);
+          p[k] = phi[k * cap + j];
+          pmax = fmaxf(pmax, fabsf(p[k]));
+        }
+        if (pmax <= 0.5f) {
+          int* a0 = acc + base;
+#pragma unroll
+          for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+            for (int cy = 0; cy < 3; ++cy) {
+              int* ar = a0 + cz * PS + cy * AX;
+#pragma unroll
+              for (int cx = 0; cx < 3; ++cx) {
+                const float pk = p[9 * cz + 3 * cy + cx];
+                atomicAdd(ar + cx, round_small(pk * q0));
+                atomicAdd(ar + ACC + cx, round_small(pk * q1));
+                atomicAdd(ar + 2 * ACC + cx, round_small(pk * q2));
+              }
+            }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 27; ++k) {
+            const int li = base + (k / 9) * PS + ((k / 3) % 3) * AX + k % 3;
+            if (fabsf(p[k]) <= 0.5f) {
+              atomicAdd(&acc[li], round_small(p[k] * q0));
+              atomicAdd(&acc[ACC + li], round_small(p[k] * q1));
+              atomicAdd(&acc[2 * ACC + li], round_small(p[k] * q2));
+            } else {
+              const int gx = wrap(i[0] + k % 3 - 1, D.n[0], D.periodic[0]);
+              const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);
+              const int gz = wrap(i[2] + k / 9 - 1, D.n[2], D.periodic[2]);
+              const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
+              add_field<float, FT>(f + o, p[k] * v[0]);
+              add_field<float, FT>(f + N + o, p[k] * v[1]);
+              add_field<float, FT>(f + 2 * N + o, p[k] * v[2]);
+            }
           }
         }
       }
       __syncthreads();
       if (VEC) {
-        const int G = AX / 4;
-        for (int g = tid; g < G * AY * AZ; g += kSpreadThreads) {
-          const int q = g % G, row = g / G;
-          const int ey = row % AY, ez = row / AY;
-          const int e = ez * PS + ey * AX + 4 * q;
-          const int4 a0 = *reinterpret_cast<const int4*>(&acc[e]);
-          const int4 a1 = *reinterpret_cast<const int4*>(&acc[ACC + e]);
-          const int4 a2 = *reinterpret_cast<const int4*>(&acc[2 * ACC + e]);
+        constexpr int G = AX / 4;
+        for (int g = tid; g < G * ROWS; g += kSpreadThreads) {
+          const int row = g / G, q = g - row * G;
+          if (!flag[row]) continue;
+          const int e = row_a[row] + 4 * q;
+          int4* p0 = reinterpret_cast<int4*>(&acc[e]);
+          int4* p1 = reinterpret_cast<int4*>(&acc[ACC + e]);
+          int4* p2 = reinterpret_cast<int4*>(&acc[2 * ACC + e]);
+          const int4 a0 = *p0, a1 = *p1, a2 = *p2;
           const bool n0 = (a0.x | a0.y | a0.z | a0.w) != 0;
           const bool n1 = (a1.x | a1.y | a1.z | a1.w) != 0;
           const bool n2 = (a2.x | a2.y | a2.z | a2.w) != 0;
           if (!(n0 || n1 || n2)) continue;
+          const int4 z = make_int4(0, 0, 0, 0);
+          *p0 = z;
+          *p1 = z;
+          *p2 = z;
           int gx = ox - XOFF + 4 * q;
           if (gx < 0 || gx >= D.n[0]) {
             if (!D.periodic[0]) continue;
             gx = gx < 0 ? gx + D.n[0] : gx - D.n[0];
             if (gx < 0 || gx >= D.n[0]) continue;        // padding beyond one period holds no sums
           }
-          const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
-          const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
-          float* fo = reinterpret_cast<float*>(f) + ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
+          float* fo = reinterpret_cast<float*>(f) + (int64_t)row_g[row] * D.n[0] + gx;
           const float u0 = inv_scale[0], u1 = inv_scale[1], u2 = inv_scale[2];
           if (n0) red_add_v4(fo, a0.x * u0, a0.y * u0, a0.z * u0, a0.w * u0);
           if (n1) red_add_v4(fo + N, a1.x * u1, a1.y * u1, a1.z * u1, a1.w * u1);
           if (n2) red_add_v4(fo + 2 * N, a2.x * u2, a2.y * u2, a2.z * u2, a2.w * u2);
         }
       } else {
-        for (int e = tid; e < ACC; e += kSpreadThreads) {
-          const int ez = e / PS, r = e - ez * PS;
-          if (r >= AY * AX) continue;                    // plane padding
-          const int a0 = acc[e], a1 = acc[ACC + e], a2 = acc[2 * ACC + e];
-          if ((a0 | a1 | a2) != 0) {
-            const int ey = r / AX, ex2 = r - ey * AX;
-            const int gx = wrap(ox - XOFF + ex2, D.n[0], D.periodic[0]);
-            const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
-            const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
-            const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
-            if (a0) add_field<float, FT>(f + o, a0 * inv_scale[0]);
-            if (a1) add_field<float, FT>(f + N + o, a1 * inv_scale[1]);
-            if (a2) add_field<float, FT>(f + 2 * N + o, a2 * inv_scale[2]);
-          }
+        for (int e = tid; e < AX * ROWS; e += kSpreadThreads) {
+          const int row = e / AX, ex = e - row * AX;
+          if (!flag[row]) continue;
+          const int li = row_a[row] + ex;
+          const int a0 = acc[li], a1 = acc[ACC + li], a2 = acc[2 * ACC + li];
+          if ((a0 | a1 | a2) == 0) continue;
+          acc[li] = 0;
+          acc[ACC + li] = 0;
+          acc[2 * ACC + li] = 0;
+          const int gx = wrap(ox - XOFF + ex, D.n[0], D.periodic[0]);
+          const int64_t o = (int64_t)row_g[row] * D.n[0] + gx;
+          if (a0) add_field<float, FT>(f + o, a0 * inv_scale[0]);
+          if (a1) add_field<float, FT>(f + N + o, a1 * inv_scale[1]);
+          if (a2) add_field<float, FT>(f + 2 * N + o, a2 * inv_scale[2]);
         }
       }
       __syncthreads();
+      for (int r = tid; r < ROWS; r += kSpreadThreads) flag[r] = 0;
     }
   }
 }
@@ -365,6 +425,8 @@ static Dims dims_of(const mls_ctx* ctx) {
     D.n[d] = ctx->n[d];
     D.periodic[d] = ctx->periodic[d];
   }
+  D.div0.init(ctx->n[0]);
+  D.div1.init(ctx->n[1]);
   return D;
 }
 
@@ -395,17 +457,29 @@ static cudaError_t configure_kernel(mls_ctx* ctx, K kernel, int smem) {
   return cudaSuccess;
 }
 
+template <typename FT, bool VEC>
+static const void* spread_kernel(int lx) {
+  switch (lx) {
+    case 1: return VEC ? nullptr : (const void*)k_spread<FT, false, 1>;
+    case 2: return (const void*)k_spread<FT, VEC, 2>;
+    case 3: return (const void*)k_spread<FT, VEC, 3>;
+    case 4: return (const void*)k_spread<FT, VEC, 4>;
+    default: return (const void*)k_spread<FT, VEC, 5>;
+  }
+}
+
 cudaError_t spread_configure(mls_ctx* ctx) {
   const int smem = (int)spread_smem_bytes(ctx);
+  const int lx = ctx->tiles.l[0];
   if (ctx->opt.real == MLS_F64) return configure_kernel(ctx, k_spread_f64, smem);
-  if (ctx->opt.field == MLS_BF16) return configure_kernel(ctx, k_spread<__nv_bfloat16, false>, smem);
+  if (ctx->opt.field == MLS_BF16) return configure_kernel(ctx, spread_kernel<__nv_bfloat16, false>(lx), smem);
   if (spread_vec(ctx)) {
     // The scalar variant also runs when f is not 16-byte aligned (same layout size or smaller).
-    cudaError_t e = configure_kernel(ctx, k_spread<float, false>, smem);
+    cudaError_t e = configure_kernel(ctx, spread_kernel<float, false>(lx), smem);
     if (e != cudaSuccess) return e;
-    return configure_kernel(ctx, k_spread<float, true>, smem);
+    return configure_kernel(ctx, spread_kernel<float, true>(lx), smem);
   }
-  return configure_kernel(ctx, k_spread<float, false>, smem);
+  return configure_kernel(ctx, spread_kernel<float, false>(lx), smem);
 }
 
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s) {
@@ -425,10 +499,17 @@ cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void*
 }
 
 template <typename FT, bool VEC>
-static void launch_spread_one(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s) {
-  k_spread<FT, VEC><<<ctx->spread_grid, ctx->spread_threads, spread_smem_bytes(ctx), s>>>(
-      dims_of(ctx), ctx->tiles, (const float*)T->phi, (const float*)T->c, T->home, T->perm, T->items, T->n_items,
-      T->offsets, T->counts, T->M, T->cap, (const float*)F, (FT*)f);
+static cudaError_t launch_spread_one(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f,
+                                     cudaStream_t s) {
+  Dims D = dims_of(ctx);
+  Tiles tl = ctx->tiles;
+  const float* phi = (const float*)T->phi;
+  const float* c = (const float*)T->c;
+  int64_t M = T->M, cap = T->cap;
+  void* args[] = {&D, &tl, (void*)&phi, (void*)&c, (void*)&T->home, (void*)&T->perm, (void*)&T->items,
+                  (void*)&T->n_items, (void*)&T->offsets, (void*)&T->counts, &M, &cap, (void*)&F, &f};
+  return cudaLaunchKernel(spread_kernel<FT, VEC>(tl.l[0]), dim3(ctx->spread_grid), dim3(ctx->spread_threads), args,
+                          spread_smem_bytes(ctx), s);
 }
 
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s) {
@@ -437,9 +518,10 @@ cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void*
     k_spread_f64<<<ctx->spread_grid, kSpreadThreads, spread_smem_bytes(ctx), s>>>(
         dims_of(ctx), ctx->tiles, (const double*)T->phi, (const double*)T->c, T->home, T->perm, T->items,
         T->n_items, T->offsets, T->counts, T->M, T->cap, (const double*)F, (double*)f);
-  else if (ctx->opt.field == MLS_BF16) launch_spread_one<__nv_bfloat16, false>(ctx, T, F, f, s);
-  else if (spread_vec(ctx) && (reinterpret_cast<uintptr_t>(f) & 15) == 0) launch_spread_one<float, true>(ctx, T, F, f, s);
-  else launch_spread_one<float, false>(ctx, T, F, f, s);
+  else if (ctx->opt.field == MLS_BF16) return launch_spread_one<__nv_bfloat16, false>(ctx, T, F, f, s);
+  else if (spread_vec(ctx) && (reinterpret_cast<uintptr_t>(f) & 15) == 0)
+    return launch_spread_one<float, true>(ctx, T, F, f, s);
+  else return launch_spread_one<float, false>(ctx, T, F, f, s);
   return cudaGetLastError();
 }
 
