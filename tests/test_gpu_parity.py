@@ -206,6 +206,30 @@ def test_crowded_tile(api):
     _compare(g, r, TOL["f32"])
 
 
+@pytest.mark.parametrize("nx", [21, 22])
+def test_uneven_x_extent(api, nx):
+    """n_x odd (scalar-load interpolation, scalar flush) and n_x = 2 mod 4 (paired loads, scalar flush),
+    with markers on both periodic x seams."""
+    rng = np.random.default_rng(nx)
+    faces = [uniform_faces(nx), uniform_faces(16), uniform_faces(12)]
+    periodic = (True, True, True)
+    grid = oracle.Grid(faces, periodic)
+    M = 4000
+    x = np.stack([rng.uniform(-1, 1, M) for _ in range(3)])
+    x[0, :200] = rng.uniform(faces[0][0], faces[0][1], 200)         # home cell x = 0
+    x[0, 200:400] = rng.uniform(faces[0][nx - 1], faces[0][nx], 200)  # home cell x = n_x - 1
+    x = x.astype(np.float32)
+    x[0] = np.minimum(x[0], _below(faces[0][nx], "f32"))
+    area = rng.uniform(0.5, 1.5, M).astype(np.float32) * (2.0 / 16) ** 2
+    u = rng.normal(size=(3, 12, 16, nx)).astype(np.float32)
+    F = rng.normal(size=(3, M)).astype(np.float32)
+    ctx = api.Context(faces, periodic, real="f32", brick_log2=(2, 2, 2))
+    g = run_gpu(ctx, x, area, "exact", torch.as_tensor(u, device=DEV), F)
+    r = run_oracle(grid, x, area, "exact", u, F)
+    assert g["status"]["dropped"] == 0
+    _compare(g, r, TOL["f32"])
+
+
 @pytest.mark.parametrize("brick", [(1, 1, 1), (2, 3, 4), (5, 5, 1)])
 def test_tile_shapes(api, brick):
     w = make_workload("c2", n=64, n_bodies=12)
