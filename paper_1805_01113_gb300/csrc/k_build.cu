@@ -2,6 +2,8 @@
 // shape functions on the sub-Eulerian mesh, and fast-MLS (Eqs. 9-10).
 // One thread per marker, markers visited in tile order (perm), so phi[k][j],
 // c[j] and home[j] are written with unit stride across a warp.
+#include <algorithm>
+
 #include "mls_host.h"
 
 namespace mls {
@@ -18,6 +20,7 @@ struct BuildArgs {
   R* c;
   int32_t* home;
   unsigned long long* status;
+  int32_t* redo;         // markers whose single-precision solve is redone in double (count in status[2])
   R inv_eps2;
   double inv_eps2_d;
   int refine;
@@ -64,8 +67,10 @@ __device__ __forceinline__ void marker_finish(const BuildArgs<R>& a, int64_t j, 
 }
 
 // Exact-MLS build (Eqs. 3-6, 8): phi is written node by node as it is formed.
+// A single-precision solve that is ill-conditioned (cond_1(A) > cond_max) or
+// not numerically SPD queues the marker for k_build_exact_redo instead.
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_build_exact(BuildArgs<R> a) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact(BuildArgs<R> a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.M) return;
   int h[3];
@@ -76,32 +81,51 @@ __global__ void __launch_bounds__(kBlock) k_build_exact(BuildArgs<R> a) {
   R cond = R(0);
   const bool want_cond = sizeof(R) == 4 && a.cond_max > 0.0;
   bool good = exact_solve<R>(s, a.inv_eps2, a.refine, w, y, want_cond ? &cond : nullptr);
-  ScaleSums<R> sums;
   if (sizeof(R) == 4 && (!good || (want_cond && (double)cond > a.cond_max))) {
-    // Ill-conditioned (or not numerically SPD) in single precision: redo the
-    // marker in double and round the result.
-    AxisNodes<double> sd[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) sd[d] = axis_nodes(a.gd.ax[d], h[d], (double)p[d]);
-    double wd[3][3], yd[4];
-    good = exact_solve<double>(sd, a.inv_eps2_d, 0, wd, yd, nullptr);
-    if (good)
-      exact_emit(sd, wd, yd, [&](int q, int b, int c, double v) {
-        a.phi[(9 * c + 3 * b + q) * a.cap + j] = (R)v;
-        sums.add(s, q, b, c, (R)v);
-      });
-    atomicAdd(&a.status[2], 1ULL);
-  } else if (good) {
+    a.redo[atomicAdd(&a.status[2], 1ULL)] = (int32_t)j;
+    return;
+  }
+  ScaleSums<R> sums;
+  if (good) {
     exact_emit(s, w, y, [&](int q, int b, int c, R v) {
       a.phi[(9 * c + 3 * b + q) * a.cap + j] = v;
       sums.add(s, q, b, c, v);
     });
-  }
-  if (!good) {
+  } else {
 #pragma unroll
     for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = R(0);
   }
   marker_finish(a, j, h, s, sums, ar);
+}
+
+// The queued single-precision markers, solved in double and rounded
+// (grid-stride over the queue that k_build_exact filled).
+__global__ void __launch_bounds__(kBlock) k_build_exact_redo(BuildArgs<float> a) {
+  const unsigned long long n = a.status[2];
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const int64_t j = a.redo[q];
+    int h[3];
+    float p[3], ar;
+    AxisNodes<float> s[3];
+    if (!marker_setup(a, j, h, p, s, ar)) continue;
+    AxisNodes<double> sd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sd[d] = axis_nodes(a.gd.ax[d], h[d], (double)p[d]);
+    double wd[3][3], yd[4];
+    const bool good = exact_solve<double>(sd, a.inv_eps2_d, 0, wd, yd, nullptr);
+    ScaleSums<float> sums;
+    if (good) {
+      exact_emit(sd, wd, yd, [&](int qq, int b, int c, double v) {
+        a.phi[(9 * c + 3 * b + qq) * a.cap + j] = (float)v;
+        sums.add(s, qq, b, c, (float)v);
+      });
+    } else {
+#pragma unroll
+      for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = 0.f;
+    }
+    marker_finish(a, j, h, s, sums, ar);
+  }
 }
 
 // Fast-MLS: the marker's position in its home cell picks the enclosing
@@ -223,6 +247,7 @@ static BuildArgs<R> make_args(const mls_ctx* ctx, mls_transfer* T, const void* x
   a.c = (R*)T->c;
   a.home = T->home;
   a.status = T->status;
+  a.redo = T->key;  // free once the tile sort has scattered
   a.inv_eps2 = (R)(1.0 / (ctx->opt.eps * ctx->opt.eps));
   a.inv_eps2_d = 1.0 / (ctx->opt.eps * ctx->opt.eps);
   a.refine = ctx->opt.real == MLS_F32 ? ctx->opt.refine : 0;
@@ -238,8 +263,12 @@ cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* 
   const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
   if (ctx->opt.real == MLS_F64)
     k_build_exact<double><<<grid, kBlock, 0, s>>>(make_args<double>(ctx, T, x, area, M));
-  else
-    k_build_exact<float><<<grid, kBlock, 0, s>>>(make_args<float>(ctx, T, x, area, M));
+  else {
+    const BuildArgs<float> a = make_args<float>(ctx, T, x, area, M);
+    k_build_exact<float><<<grid, kBlock, 0, s>>>(a);
+    const unsigned redo_grid = (unsigned)std::min<int64_t>(grid, 4 * 152);
+    k_build_exact_redo<<<redo_grid, kBlock, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
