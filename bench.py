@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--bodies", type=int, default=None, help="number of bodies (smaller profiling cases)")
     p.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--tiles", default=None, help="spreading tile log2 sizes, e.g. 3,3,2 (skips the autotuner)")
     p.add_argument("--no-surrogate", action="store_true")
     return p.parse_args()
 
@@ -271,7 +272,9 @@ def run_ours(a, rank, world, local):
     # Spreading tile shape: autotuned on this workload (exact-MLS step), else 8x8x8.
     tiles, tune_ms = (3, 3, 3), None
     api.Context(w.faces, w.periodic, real=real).marker_prep(V, tri, x, area)
-    if not a.no_autotune:
+    if a.tiles:
+        tiles = tuple(int(t) for t in a.tiles.split(","))
+    elif not a.no_autotune:
         tiles, tune_ms = autotune.tune(w.faces, w.periodic, x, area, u, F, "exact", real)
     ctx = api.Context(w.faces, w.periodic, real=real, brick_log2=tiles)
     T = ctx.transfer(M)

@@ -44,9 +44,9 @@ __device__ __forceinline__ void decode_home(int32_t h, const Dims& D, int i[3]) 
   i[1] = r - i[2] * D.n[1];
 }
 
-// U_l = sum_k phi_k^l u_k for the 3 components (text after Eq. 6).  One
-// thread per stored marker; the 27 phi values are read with unit stride
-// across the warp, the field through the read-only path.
+// U_l = sum_k phi_k^l u_k for the 3 components (text after Eq. 6), double
+// precision.  One thread per stored marker; the 27 phi values are read with
+// unit stride across the warp, the field through the read-only path.
 template <typename R, typename FT>
 __global__ void __launch_bounds__(kBlock) k_interp(Dims D, const R* __restrict__ phi, const int32_t* __restrict__ home,
                                                    const int32_t* __restrict__ perm, int64_t M, int64_t cap,
@@ -91,77 +91,142 @@ __global__ void __launch_bounds__(kBlock) k_interp(Dims D, const R* __restrict__
   U[2 * M + m] = s2;
 }
 
-// Single-precision interpolation with paired loads: for a home cell i_x in
-// [1, n_x - 2] the three x-neighbours i_x - 1 .. i_x + 1 of a row lie in the
-// two aligned float2 at a = (i_x - 1) & ~1 (needs n_x even and u 8-byte
-// aligned), so each row and component takes two 8-byte loads instead of
-// three 4-byte ones.  Home cells on a periodic x edge wrap and take the
-// scalar form.
-__global__ void __launch_bounds__(kBlock) k_interp_pair(Dims D, const float* __restrict__ phi,
-                                                        const int32_t* __restrict__ home,
-                                                        const int32_t* __restrict__ perm, int64_t M, int64_t cap,
-                                                        const float* __restrict__ u, float* __restrict__ U) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= M) return;
-  const int64_t m = perm[j];
-  const int32_t h = home[j];
-  if (h < 0) {
+// Asynchronous 4-byte global-to-shared copy (no register round trip).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void stage_cell(float* dst, int stride, const float* u, int64_t N, int64_t o) {
+  cp_async4(dst, u + o);
+  cp_async4(dst + stride, u + N + o);
+  cp_async4(dst + 2 * stride, u + 2 * N + o);
+}
+__device__ __forceinline__ void stage_cell(float* dst, int stride, const __nv_bfloat16* u, int64_t N, int64_t o) {
+  const float v0 = __bfloat162float(u[o]), v1 = __bfloat162float(u[N + o]), v2 = __bfloat162float(u[2 * N + o]);
+  dst[0] = v0;
+  dst[stride] = v1;
+  dst[2 * stride] = v2;
+}
+
+// Field brick of a spreading tile for interpolation: the tile plus a
+// one-cell halo, rows of BX = 2^lx + 2 cells, BY rows per plane, BZ planes of
+// stride PS (padded by 4 cells against bank aliasing), three components;
+// then per brick row its offset in the brick, its global row index and a
+// touched flag.
+struct InterpSmem {
+  int BX, BY, BZ, PS, CELLS, ROWS, rows, total;
+  __host__ __device__ InterpSmem(int lx, int ly, int lz) {
+    BX = (1 << lx) + 2;
+    BY = (1 << ly) + 2;
+    BZ = (1 << lz) + 2;
+    PS = BY * BX + 4;
+    CELLS = BZ * PS;
+    ROWS = BY * BZ;
+    rows = (3 * CELLS * 4 + 15) & ~15;
+    total = (rows + 8 * ROWS + ROWS + 15) & ~15;
+  }
+};
+
+// U_l = sum_k phi_k^l u_k (text after Eq. 6), single precision, by spreading
+// tile.  Persistent blocks walk the non-empty tiles; for a tile each marker
+// flags the 9 brick rows (y, z) its support touches, the block copies the
+// flagged rows of the three field components into shared memory with
+// asynchronous copies, then each thread gathers its markers' 27 x 3 values
+// from shared memory.  Blocks then zero U of the dropped markers (the last
+// bin of the tile sort).
+template <typename FT, int LX>
+__global__ void __launch_bounds__(kInterpThreads) k_interp_brick(
+    Dims D, Tiles tl, const float* __restrict__ phi, const int32_t* __restrict__ home,
+    const int32_t* __restrict__ perm, const int32_t* __restrict__ items, const int32_t* __restrict__ n_items_p,
+    const int32_t* __restrict__ offsets, const int32_t* __restrict__ counts, int64_t M, int64_t cap,
+    const FT* __restrict__ u, float* __restrict__ U) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BX = (1 << LX) + 2;
+  const InterpSmem L(LX, tl.l[1], tl.l[2]);
+  const int BY = L.BY, PS = L.PS, CELLS = L.CELLS, ROWS = L.ROWS;
+  float* su = reinterpret_cast<float*>(smem_raw);
+  int* row_s = reinterpret_cast<int*>(smem_raw + L.rows);
+  int* row_g = row_s + ROWS;
+  unsigned char* flag = reinterpret_cast<unsigned char*>(row_g + ROWS);
+  const int tid = threadIdx.x;
+  const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
+  const int n_items = *n_items_p;
+  for (int r = tid; r < ROWS; r += kInterpThreads) flag[r] = 0;
+  __syncthreads();
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int b = items[it];
+    const int start = offsets[b], end = start + counts[b];
+    const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
+    const int ox = bx << LX, oy = by << tl.l[1], oz = bz << tl.l[2];
+    for (int j = start + tid; j < end; j += kInterpThreads) {
+      int i[3];
+      decode_home(home[j], D, i);
+      const int r0 = (i[2] - oz) * BY + (i[1] - oy);
+#pragma unroll
+      for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy) flag[r0 + cz * BY + cy] = 1;
+    }
+    for (int r = tid; r < ROWS; r += kInterpThreads) {
+      const int ey = r % BY, ez = r / BY;
+      row_s[r] = ez * PS + ey * BX;
+      row_g[r] = wrap(oz - 1 + ez, D.n[2], D.periodic[2]) * D.n[1] + wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
+    }
+    __syncthreads();
+    for (int e = tid; e < ROWS * BX; e += kInterpThreads) {
+      const int r = e / BX, ex = e - r * BX;
+      if (!flag[r]) continue;
+      const int gx = wrap(ox - 1 + ex, D.n[0], D.periodic[0]);
+      stage_cell(su + row_s[r] + ex, CELLS, u, N, (int64_t)row_g[r] * D.n[0] + gx);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int r = tid; r < ROWS; r += kInterpThreads) flag[r] = 0;
+    for (int j = start + tid; j < end; j += kInterpThreads) {
+      int i[3];
+      decode_home(home[j], D, i);
+      const int base = (i[2] - oz) * PS + (i[1] - oy) * BX + (i[0] - ox);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+          for (int cx = 0; cx < 3; ++cx) {
+            const float p = phi[(9 * cz + 3 * cy + cx) * cap + j];
+            const int si = base + cz * PS + cy * BX + cx;
+            s0 += p * su[si];
+            s1 += p * su[CELLS + si];
+            s2 += p * su[2 * CELLS + si];
+          }
+      const int64_t m = perm[j];
+      U[m] = s0;
+      U[M + m] = s1;
+      U[2 * M + m] = s2;
+    }
+    __syncthreads();
+  }
+  // Dropped markers (last bin) interpolate to zero.
+  const int64_t d0 = offsets[tl.nbins - 1];
+  for (int64_t j = d0 + (int64_t)blockIdx.x * kInterpThreads + tid; j < M; j += (int64_t)gridDim.x * kInterpThreads) {
+    const int64_t m = perm[j];
     U[m] = 0.f;
     U[M + m] = 0.f;
     U[2 * M + m] = 0.f;
-    return;
   }
-  int i[3];
-  decode_home(h, D, i);
-  int ys[3], zs[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    ys[a] = wrap(i[1] + a - 1, D.n[1], D.periodic[1]);
-    zs[a] = wrap(i[2] + a - 1, D.n[2], D.periodic[2]);
+}
+
+template <typename FT>
+static const void* interp_kernel(int lx) {
+  switch (lx) {
+    case 1: return (const void*)k_interp_brick<FT, 1>;
+    case 2: return (const void*)k_interp_brick<FT, 2>;
+    case 3: return (const void*)k_interp_brick<FT, 3>;
+    case 4: return (const void*)k_interp_brick<FT, 4>;
+    default: return (const void*)k_interp_brick<FT, 5>;
   }
-  const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  if (i[0] >= 1 && i[0] <= D.n[0] - 2) {
-    const int a0 = (i[0] - 1) & ~1;
-    const bool odd = ((i[0] - 1) & 1) != 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float* r = u + ((int64_t)zs[c] * D.n[1] + ys[b]) * D.n[0] + a0;
-        const int k = 9 * c + 3 * b;
-        const float p0 = phi[k * cap + j], p1 = phi[(k + 1) * cap + j], p2 = phi[(k + 2) * cap + j];
-        float2 lo = __ldg(reinterpret_cast<const float2*>(r)), hi = __ldg(reinterpret_cast<const float2*>(r + 2));
-        s0 += p0 * (odd ? lo.y : lo.x) + p1 * (odd ? hi.x : lo.y) + p2 * (odd ? hi.y : hi.x);
-        lo = __ldg(reinterpret_cast<const float2*>(r + N));
-        hi = __ldg(reinterpret_cast<const float2*>(r + N + 2));
-        s1 += p0 * (odd ? lo.y : lo.x) + p1 * (odd ? hi.x : lo.y) + p2 * (odd ? hi.y : hi.x);
-        lo = __ldg(reinterpret_cast<const float2*>(r + 2 * N));
-        hi = __ldg(reinterpret_cast<const float2*>(r + 2 * N + 2));
-        s2 += p0 * (odd ? lo.y : lo.x) + p1 * (odd ? hi.x : lo.y) + p2 * (odd ? hi.y : hi.x);
-      }
-  } else {
-    int xs[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) xs[a] = wrap(i[0] + a - 1, D.n[0], D.periodic[0]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const int64_t row = ((int64_t)zs[c] * D.n[1] + ys[b]) * D.n[0];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float p = phi[(9 * c + 3 * b + a) * cap + j];
-          const int64_t o = row + xs[a];
-          s0 += p * __ldg(u + o);
-          s1 += p * __ldg(u + N + o);
-          s2 += p * __ldg(u + 2 * N + o);
-        }
-      }
-  }
-  U[m] = s0;
-  U[M + m] = s1;
-  U[2 * M + m] = s2;
 }
 
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
@@ -541,7 +606,26 @@ static const void* spread_kernel(int lx) {
   }
 }
 
+static cudaError_t interp_configure(mls_ctx* ctx) {
+  if (ctx->opt.real == MLS_F64) return cudaSuccess;
+  const int smem = InterpSmem(ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2]).total;
+  const void* k = ctx->opt.field == MLS_F32 ? interp_kernel<float>(ctx->tiles.l[0])
+                                            : interp_kernel<__nv_bfloat16>(ctx->tiles.l[0]);
+  cudaError_t e;
+  if (smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kInterpThreads, smem)) != cudaSuccess) return e;
+  ctx->interp_grid = (per_sm > 0 ? per_sm : 1) * sms;
+  return cudaSuccess;
+}
+
 cudaError_t spread_configure(mls_ctx* ctx) {
+  const cudaError_t ei = interp_configure(ctx);
+  if (ei != cudaSuccess) return ei;
   const int smem = (int)spread_smem_bytes(ctx);
   const int lx = ctx->tiles.l[0];
   if (ctx->opt.real == MLS_F64) return configure_kernel(ctx, k_spread_f64, smem);
@@ -562,15 +646,16 @@ cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void*
   if (ctx->opt.real == MLS_F64)
     k_interp<double, double><<<grid, kBlock, 0, s>>>(D, (const double*)T->phi, T->home, T->perm, T->M, T->cap,
                                                      (const double*)u, (double*)U);
-  else if (ctx->opt.field == MLS_F32 && D.n[0] % 2 == 0 && (reinterpret_cast<uintptr_t>(u) & 7) == 0)
-    k_interp_pair<<<grid, kBlock, 0, s>>>(D, (const float*)T->phi, T->home, T->perm, T->M, T->cap, (const float*)u,
-                                          (float*)U);
-  else if (ctx->opt.field == MLS_F32)
-    k_interp<float, float><<<grid, kBlock, 0, s>>>(D, (const float*)T->phi, T->home, T->perm, T->M, T->cap,
-                                                   (const float*)u, (float*)U);
-  else
-    k_interp<float, __nv_bfloat16><<<grid, kBlock, 0, s>>>(D, (const float*)T->phi, T->home, T->perm, T->M,
-                                                           T->cap, (const __nv_bfloat16*)u, (float*)U);
+  else {
+    Tiles tl = ctx->tiles;
+    const float* phi = (const float*)T->phi;
+    int64_t M = T->M, cap = T->cap;
+    void* args[] = {(void*)&D, &tl, (void*)&phi, (void*)&T->home, (void*)&T->perm, (void*)&T->items,
+                    (void*)&T->n_items, (void*)&T->offsets, (void*)&T->counts, &M, &cap, (void*)&u, &U};
+    const void* k = ctx->opt.field == MLS_F32 ? interp_kernel<float>(tl.l[0]) : interp_kernel<__nv_bfloat16>(tl.l[0]);
+    return cudaLaunchKernel(k, dim3(ctx->interp_grid), dim3(kInterpThreads), args,
+                            (size_t)InterpSmem(tl.l[0], tl.l[1], tl.l[2]).total, s);
+  }
   return cudaGetLastError();
 }
 

@@ -42,6 +42,7 @@ struct mls_ctx {
   // Persistent grid of the spreading kernel (blocks resident on the device).
   int spread_grid;
   int spread_threads;
+  int interp_grid;       // persistent grid of the tile-organised interpolation
   // Learned surrogate: float32 parameters and the packed bfloat16 copy.
   float* mlp_theta;
   unsigned char* mlp_pack;
@@ -78,6 +79,7 @@ constexpr int kScanTile = 4096;       // bins per scan tile
 constexpr int kScanMaxTiles = 8192;   // bins <= 32 Mi
 constexpr int kBlock = 256;           // threads per block of the per-marker kernels
 constexpr int kSpreadThreads = 128;   // threads per block of the spreading kernel
+constexpr int kInterpThreads = 128;   // threads per block of the tile-organised interpolation
 
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
