@@ -433,13 +433,19 @@ __global__ void __launch_bounds__(kMlpThreads) k_build_surrogate(SurrogateArgs a
   }
   float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (ok) {
+    // Spacing features of the class axis c and the reference axis u
+    // (selected without indexing the node array by a runtime axis).
+    const int c = a.ax.c, u = a.ax.u;
+    const float wc0 = c == 0 ? s[0].w[0] : (c == 1 ? s[1].w[0] : s[2].w[0]);
+    const float wc1 = c == 0 ? s[0].w[1] : (c == 1 ? s[1].w[1] : s[2].w[1]);
+    const float wc2 = c == 0 ? s[0].w[2] : (c == 1 ? s[1].w[2] : s[2].w[2]);
+    const float wu1 = u == 0 ? s[0].w[1] : (u == 1 ? s[1].w[1] : s[2].w[1]);
     f[0] = s[0].t;
     f[1] = s[1].t;
     f[2] = s[2].t;
-    const AxisNodes<float>& sc = s[a.ax.c];
-    f[3] = logf(sc.w[0] / sc.w[1]);
-    f[4] = logf(sc.w[2] / sc.w[1]);
-    f[5] = logf(sc.w[1] / s[a.ax.u].w[1]);
+    f[3] = logf(wc0 / wc1);
+    f[4] = logf(wc2 / wc1);
+    f[5] = logf(wc1 / wu1);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) feat[lane * 8 + i] = f[i];

@@ -229,8 +229,16 @@ static const void* interp_kernel(int lx) {
   }
 }
 
+// Adds four consecutive cells of a field with one vector reduction:
+// 16 bytes of float, or 8 bytes (two bf16x2 pairs) of bfloat16.
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void red_add_v4(__nv_bfloat16* p, float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  asm volatile("red.global.add.noftz.v2.bf16x2 [%0], {%1, %2};" ::"l"(p),
+               "r"(*reinterpret_cast<const unsigned*>(&lo)), "r"(*reinterpret_cast<const unsigned*>(&hi))
                : "memory");
 }
 
@@ -467,7 +475,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
             gx = gx < 0 ? gx + D.n[0] : gx - D.n[0];
             if (gx < 0 || gx >= D.n[0]) continue;        // padding beyond one period holds no sums
           }
-          float* fo = reinterpret_cast<float*>(f) + (int64_t)row_g[row] * D.n[0] + gx;
+          FT* fo = f + (int64_t)row_g[row] * D.n[0] + gx;
           const float u0 = inv_scale[0], u1 = inv_scale[1], u2 = inv_scale[2];
           if (n0) red_add_v4(fo, a0.x * u0, a0.y * u0, a0.z * u0, a0.w * u0);
           if (n1) red_add_v4(fo + N, a1.x * u1, a1.y * u1, a1.z * u1, a1.w * u1);
@@ -568,10 +576,13 @@ static Dims dims_of(const mls_ctx* ctx) {
   return D;
 }
 
-// The vector flush needs float fields, 4-aligned tile columns (l_x >= 2) and
-// an x extent that is a multiple of 4 (so a wrapped group stays aligned).
-static bool spread_vec(const mls_ctx* ctx) {
-  return ctx->opt.field == MLS_F32 && ctx->tiles.l[0] >= 2 && ctx->n[0] % 4 == 0;
+// The vector flush needs 4-aligned tile columns (l_x >= 2) and an x extent
+// that is a multiple of 4 (so a wrapped group stays aligned); the field must
+// start on a 16-byte (float) or 8-byte (bfloat16) boundary.
+static bool spread_vec(const mls_ctx* ctx) { return ctx->tiles.l[0] >= 2 && ctx->n[0] % 4 == 0; }
+static bool spread_vec_aligned(const mls_ctx* ctx, const void* f) {
+  const uintptr_t mask = ctx->opt.field == MLS_F32 ? 15 : 7;
+  return spread_vec(ctx) && (reinterpret_cast<uintptr_t>(f) & mask) == 0;
 }
 
 size_t spread_smem_bytes(const mls_ctx* ctx) {
@@ -629,14 +640,15 @@ cudaError_t spread_configure(mls_ctx* ctx) {
   const int smem = (int)spread_smem_bytes(ctx);
   const int lx = ctx->tiles.l[0];
   if (ctx->opt.real == MLS_F64) return configure_kernel(ctx, k_spread_f64, smem);
-  if (ctx->opt.field == MLS_BF16) return configure_kernel(ctx, spread_kernel<__nv_bfloat16, false>(lx), smem);
+  const bool bf = ctx->opt.field == MLS_BF16;
   if (spread_vec(ctx)) {
-    // The scalar variant also runs when f is not 16-byte aligned (same layout size or smaller).
-    cudaError_t e = configure_kernel(ctx, spread_kernel<float, false>(lx), smem);
+    // The scalar variant also runs when f is not aligned for the vector reductions (same layout size or smaller).
+    cudaError_t e = configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, false>(lx) : spread_kernel<float, false>(lx),
+                                     smem);
     if (e != cudaSuccess) return e;
-    return configure_kernel(ctx, spread_kernel<float, true>(lx), smem);
+    return configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, true>(lx) : spread_kernel<float, true>(lx), smem);
   }
-  return configure_kernel(ctx, spread_kernel<float, false>(lx), smem);
+  return configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, false>(lx) : spread_kernel<float, false>(lx), smem);
 }
 
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s) {
@@ -679,8 +691,10 @@ cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void*
     k_spread_f64<<<ctx->spread_grid, kSpreadThreads, spread_smem_bytes(ctx), s>>>(
         dims_of(ctx), ctx->tiles, (const double*)T->phi, (const double*)T->c, T->home, T->perm, T->items,
         T->n_items, T->offsets, T->counts, T->M, T->cap, (const double*)F, (double*)f);
-  else if (ctx->opt.field == MLS_BF16) return launch_spread_one<__nv_bfloat16, false>(ctx, T, F, f, s);
-  else if (spread_vec(ctx) && (reinterpret_cast<uintptr_t>(f) & 15) == 0)
+  else if (ctx->opt.field == MLS_BF16)
+    return spread_vec_aligned(ctx, f) ? launch_spread_one<__nv_bfloat16, true>(ctx, T, F, f, s)
+                                      : launch_spread_one<__nv_bfloat16, false>(ctx, T, F, f, s);
+  else if (spread_vec_aligned(ctx, f))
     return launch_spread_one<float, true>(ctx, T, F, f, s);
   else return launch_spread_one<float, false>(ctx, T, F, f, s);
   return cudaGetLastError();

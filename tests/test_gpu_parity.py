@@ -257,15 +257,17 @@ def test_double_fallback_on_conditioning(api):
     assert run_gpu(ctx2, x, area, "exact")["status"]["refined_fp64"] == 0
 
 
-def test_bf16_fields(api):
+@pytest.mark.parametrize("brick", [(3, 3, 3), (1, 3, 3)])
+def test_bf16_fields(api, brick):
     """bfloat16 field storage with float accumulation: interpolation from identical inputs
-    stays at single-precision accuracy; the spread field is rounded to bfloat16."""
+    stays at single-precision accuracy; the spread field is rounded to bfloat16 (8-byte
+    bf16x2 vector reductions with 8x8x8 tiles, scalar ones with 2-wide tiles)."""
     w = make_workload("c2", n=64, n_bodies=12)
     grid = oracle.Grid(w.faces, w.periodic)
     x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
     u = torch.as_tensor(field_full_np(w.modes, w.faces), device=DEV).to(torch.bfloat16)
     F = w.forces().astype(np.float32)
-    ctx = api.Context(w.faces, w.periodic, real="f32", field="bf16")
+    ctx = api.Context(w.faces, w.periodic, real="f32", field="bf16", brick_log2=brick)
     g = run_gpu(ctx, x, area, "exact", u, F)
     r = run_oracle(grid, x, area, "exact", u.double().cpu().numpy(), F)
     assert normwise(g["U"], r["U"]) <= TOL["f32"]
