@@ -30,10 +30,12 @@ from .mls import (
     interpolate,
     spread,
     SparseField,
+    direct_forcing,
 )
 
 __all__ = [
     "mlp", "Grid", "marker_prep", "locate", "support", "gaussian_weight",
     "shape_exact", "shape_exact_absolute_basis", "subnode_offsets", "fast_table",
     "shape_fast", "forcing_scale", "interpolate", "spread", "SparseField",
+    "direct_forcing",
 ]

@@ -350,3 +350,18 @@ def spread(tr, c, F, n):
         contrib = (w * np.asarray(F[comp], dtype=np.float64)[good][:, None]).ravel()
         vals[comp] = np.bincount(inv.ravel(), weights=contrib, minlength=len(uk))
     return SparseField(uk, vals)
+
+
+def direct_forcing(tr, c, u, Vb, dt, n):
+    """One direct-forcing transfer (Section 2, text after Eq. 6 and Eq. 7).
+
+    U_l = Phi^T u (interpolated velocity), F_l = (V_b,l - U_l) / dt (the IBM
+    force that drives the fluid velocity at the marker to the desired V_b),
+    then f_k = sum_l c_l phi_k^l F_l.  Markers without a usable support get
+    U_l = 0 and F_l = 0 (no forcing).  Returns (U, F, SparseField).
+    """
+    U = interpolate(tr, u)
+    U[:, ~tr.sup.ok] = 0.0
+    F = (np.asarray(Vb, dtype=np.float64) - U) / dt
+    F[:, ~tr.sup.ok] = 0.0
+    return U, F, spread(tr, c, F, n)

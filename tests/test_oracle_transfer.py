@@ -119,3 +119,61 @@ def test_unusable_markers_contribute_nothing():
     assert c[1] == 0
     sp = oracle.spread(tr, c, np.ones((3, 2)), grid.n)
     assert len(sp.keys) == 27
+
+
+# ---- direct forcing (text after Eq. 6 and Eq. 7) --------------------------------
+
+@pytest.mark.parametrize("method", ["exact", "fast"])
+def test_direct_forcing_linear_field_recovers_force(method):
+    """On a linear velocity field, exact-MLS interpolation is exact, so with
+    V_b = u(x_l) + dt G_l the force is G_l; fast-MLS is exact on constants."""
+    for _, grid in _grids():
+        m = 120
+        x = _markers(grid, m)
+        tr = oracle.shape_exact(grid, x, 1.0) if method == "exact" else oracle.shape_fast(grid, x, 1.0, 9)
+        a = np.array([0.3, -1.1, 2.0])
+        B = RNG.normal(size=(3, 3)) if method == "exact" else np.zeros((3, 3))
+        u = np.stack([_field(grid, lambda X, Y, Z, i=i: a[i] + B[i, 0] * X + B[i, 1] * Y + B[i, 2] * Z)
+                      for i in range(3)])
+        dt = 2.5e-3
+        G = RNG.normal(size=(3, m))
+        Vb = a[:, None] + B @ x + dt * G
+        c = oracle.forcing_scale(tr, np.full(m, 1e-3))
+        U, F, _ = oracle.direct_forcing(tr, c, u, Vb, dt, grid.n)
+        assert np.max(np.abs(U - (a[:, None] + B @ x))) < 1e-12
+        assert np.max(np.abs(F - G)) < 1e-8            # (V_b - U)/dt: rounding of U amplified by 1/dt
+
+
+def test_direct_forcing_at_target_is_zero():
+    """V_b equal to the interpolated velocity gives no force and no field."""
+    grid = oracle.Grid([uniform_faces(10)] * 3, (True, True, True))
+    x = _markers(grid, 80, interior=0)
+    tr = oracle.shape_exact(grid, x, 1.0)
+    u = RNG.normal(size=(3,) + grid.n[::-1])
+    Vb = oracle.interpolate(tr, u)
+    c = oracle.forcing_scale(tr, np.full(80, 1e-3))
+    U, F, f = oracle.direct_forcing(tr, c, u, Vb, 0.01, grid.n)
+    assert np.array_equal(U, Vb) and np.all(F == 0) and np.all(f.values == 0)
+
+
+def test_direct_forcing_conserves_momentum_and_drops():
+    """sum_k f_k dV_k = sum_l F_l dV_l (Eq. 7) for the computed forces; a marker
+    without support gets U = F = 0 and adds nothing."""
+    n = 10
+    grid = oracle.Grid([uniform_faces(n)] * 3, (True, True, False))
+    h = 2.0 / n
+    x = _markers(grid, 200, interior=1)
+    x[:, -1] = [0.1, 0.2, -0.99]                       # wall cell z = 0: no support
+    area = RNG.uniform(0.2, 1.0, size=200) * h * h
+    tr = oracle.shape_exact(grid, x, 1.0)
+    assert not tr.sup.ok[-1] and tr.sup.ok[:-1].all()
+    c = oracle.forcing_scale(tr, area)
+    u = RNG.normal(size=(3,) + grid.n[::-1])
+    Vb = RNG.normal(size=(3, 200))
+    U, F, sp = oracle.direct_forcing(tr, c, u, Vb, 0.05, grid.n)
+    assert np.all(U[:, -1] == 0) and np.all(F[:, -1] == 0)
+    assert np.max(np.abs(F[:, :-1] - (Vb[:, :-1] - U[:, :-1]) / 0.05)) < 1e-12
+    f = sp.to_dense(grid.n)
+    lhs = f.reshape(3, -1).sum(1) * h ** 3
+    rhs = (F * area * h).sum(1)
+    assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.max(np.abs(rhs))
