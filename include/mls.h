@@ -172,6 +172,24 @@ int mls_interpolate(mls_ctx* ctx, const mls_transfer* T, const void* u, void* U,
  *   F  device, real[3][M] (caller's marker order)   f  device, field[3][nz][ny][nx] */
 int mls_spread(mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, void* stream);
 
+/* One direct-forcing transfer (text after Eq. 6, then Eq. 7): interpolate
+ * U_l = sum_k phi_k^l u_k, form the IBM force F_l = (V_b,l - U_l) / dt that
+ * drives the fluid velocity at marker l to the desired V_b,l, and spread
+ * f_k += sum_l c_l phi_k^l F_l.  In single-precision contexts this is one
+ * fused pass over the spreading tiles that reads phi once (a context whose
+ * tile does not fit one block's shared memory composes the separate
+ * kernels; double-precision contexts always do).
+ *   u   device, field[3][nz][ny][nx]         Vb  device, real[3][M] desired velocity
+ *   dt  time step (> 0)                      U   device, real[3][M] or NULL (not written)
+ *   F   device, real[3][M] output forces     f   device, field[3][nz][ny][nx], accumulated
+ * All marker arrays are in the caller's marker order.  Dropped markers get
+ * U = 0 and F = 0 and add nothing to f.  The summation order of f is not
+ * deterministic (as for mls_spread).
+ * Errors: MLS_ERR_INVALID_ARG on NULL handles or arrays with M > 0, or
+ * dt <= 0 or not finite. */
+int mls_direct_forcing(mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb, double dt,
+                       void* U, void* F, void* f, void* stream);
+
 /* Borrowed device views of the last build (no synchronisation). */
 int mls_transfer_view(const mls_transfer* T, mls_transfer_arrays* out);
 

@@ -152,6 +152,21 @@ class Context:
         B.check(self.lib.mls_spread(self.handle, T.handle, _ptr(F), _ptr(f), _stream(stream)), "mls_spread")
         return f
 
+    def direct_forcing(self, T, u, Vb, dt, f, F=None, U=None, stream=None):
+        """Fused U = Phi^T u, F = (Vb - U)/dt, f += spread(F) (mls_direct_forcing); returns (F, U or None)."""
+        _check_tensor(u, "u", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        _check_tensor(Vb, "Vb", self.real_t, (3, T.M))
+        _check_tensor(f, "f", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        if F is None:
+            F = torch.empty((3, T.M), dtype=self.real_t, device=u.device)
+        _check_tensor(F, "F", self.real_t, (3, T.M))
+        if U is not None:
+            _check_tensor(U, "U", self.real_t, (3, T.M))
+        B.check(self.lib.mls_direct_forcing(self.handle, T.handle, _ptr(u), _ptr(Vb), float(dt),
+                                            _ptr(U) if U is not None else None, _ptr(F), _ptr(f),
+                                            _stream(stream)), "mls_direct_forcing")
+        return F, U
+
     def status(self, T, stream=None):
         s = B.mls_status()
         rc = self.lib.mls_transfer_status(T.handle, _stream(stream), C.byref(s))

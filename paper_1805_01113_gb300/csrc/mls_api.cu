@@ -213,6 +213,7 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
     return invalid("mls_create: spreading tile too large for shared memory; lower brick_log2");
   }
   cudaError_t e = spread_configure(c);
+  if (e == cudaSuccess) e = force_configure(c);
   if (e == cudaSuccess) e = mlp_configure();
   if (e != cudaSuccess) {
     free_ctx(c);
@@ -404,6 +405,20 @@ int mls_spread(mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, void
   cudaError_t e = launch_spread(ctx, T, F, f, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_spread");
+  return MLS_OK;
+}
+
+int mls_direct_forcing(mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb, double dt, void* U,
+                       void* F, void* f, void* stream) {
+  if (!ctx || !T) return invalid("mls_direct_forcing: NULL handle");
+  if (T->ctx != ctx) return invalid("mls_direct_forcing: transfer belongs to another context");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return invalid("mls_direct_forcing: dt must be positive and finite");
+  if (T->M > 0 && (!u || !Vb || !F || !f)) return invalid("mls_direct_forcing: NULL field, velocity or force");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int slot = timer_begin(ctx, "direct_forcing", s);
+  cudaError_t e = launch_direct_forcing(ctx, T, u, Vb, dt, U, F, f, s);
+  timer_end(ctx, slot, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mls_direct_forcing");
   return MLS_OK;
 }
 
