@@ -46,6 +46,8 @@ def algorithmic_bytes(kernel, rs, u_cells, verts_per_marker):
         "build_surrogate": 4 + 4 * rs + 27 * rs + rs + 4,
         "interp": 27 * rs + 8 + 3 * rs * u_cells + 3 * rs,
         "spread": 27 * rs + rs + 8 + 3 * rs + 6 * rs * u_cells,
+        # phi, c, home, perm, V_b in, F and U out, touched u read, touched f read-modify-write
+        "direct_forcing": 27 * rs + rs + 8 + 3 * rs + 3 * rs + 3 * rs + 3 * rs * u_cells + 6 * rs * u_cells,
     }.get(kernel)
 
 
@@ -131,6 +133,11 @@ for rep in range(args["reps"]):
     sp = oracle.spread(tr, c, F, g.n)
     times.append(time.perf_counter() - t0)
 out = {"phi": tr.phi, "U": U, "c": c, "fk": sp.keys, "fv": sp.values}
+if args.get("dt"):
+    # direct forcing with V_b = 0 (bodies at rest): F = (V_b - U)/dt, spread on the same support
+    F_df = (0.0 - U) / args["dt"]
+    out["F_df"] = F_df
+    out["fv_df"] = oracle.spread(tr, c, F_df, g.n).values
 if args.get("fast_too") and args["method"] == "exact":
     out["phi_fast"] = oracle.shape_fast(g, x, 1.0, 9).phi
 np.savez(args["out"], **out)
@@ -138,13 +145,13 @@ print(json.dumps({"markers": int(f1 - f0), "times": times}))
 """
 
 
-def run_oracle_sample(name, method, bodies, reps, out, kw=None, fast_too=False):
+def run_oracle_sample(name, method, bodies, reps, out, kw=None, fast_too=False, dt=None):
     env = dict(os.environ)
     env["MLS_ROOT"] = ROOT
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     args = json.dumps({"workload": name, "method": method, "bodies": bodies, "reps": reps, "out": out,
-                       "kw": kw or {}, "fast_too": fast_too})
+                       "kw": kw or {}, "fast_too": fast_too, "dt": dt})
     r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, args], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
@@ -288,8 +295,17 @@ def run_ours(a, rank, world, local):
         train = {"seconds": time.perf_counter() - t0, "final_loss": loss}
         methods.append("surrogate")
 
+    # Direct forcing (interp -> F = (V_b - U)/dt -> spread, fused): bodies at rest, V_b = 0.
+    DT = 1e-3
+    Vb0 = torch.zeros((3, M), dtype=tdt, device=dev)
+    F_df = torch.empty((3, M), dtype=tdt, device=dev)
+
     def step(method):
         ctx.marker_prep(V, tri, x, area)
+        if method == "direct_forcing":
+            ctx.build_transfer(T, x, area, "exact")
+            ctx.direct_forcing(T, u, Vb0, DT, f, F=F_df, U=U)
+            return
         ctx.build_transfer(T, x, area, method)
         ctx.interpolate(T, u, U)
         ctx.spread(T, F, f)
@@ -386,6 +402,17 @@ def run_ours(a, rank, world, local):
         bname = "build_" + mth
         others[mth] = {"value": M * world / (statistics.mean(ms_o) / 1e3), "ms_per_step": statistics.mean(ms_o),
                        "build_ms": (kt_o[bname][1] / kt_o[bname][0]) if bname in kt_o else None}
+    # fused direct-forcing step: prep + exact build + one fused transfer pass
+    ms_d, _ = timed("direct_forcing", max(3, a.steps // 2), 3, False)
+    _, kt_d = timed("direct_forcing", 3, 1, True)
+    kd = kt_d["direct_forcing"][1] / kt_d["direct_forcing"][0]
+    bd = algorithmic_bytes("direct_forcing", rs, u_cells, vpm) * M
+    others["direct_forcing"] = {
+        "value": M * world / (statistics.mean(ms_d) / 1e3), "ms_per_step": statistics.mean(ms_d),
+        "step": "marker_prep + build_transfer (exact) + direct_forcing (V_b = 0, dt = 1e-3)",
+        "kernel_ms": kd, "algorithmic_bytes_per_launch": bd, "achieved_gbs": bd / (kd / 1e3) / 1e9,
+        "frac": bd / (kd / 1e3) / 1e9 / pk["hbm_gbs"],
+        "separate_interp_spread_ms": per_launch.get("interp", 0.0) + per_launch.get("spread", 0.0)}
     if "surrogate" in others:
         step("surrogate")
         others["surrogate"]["fallback_rate"] = ctx.status(T)["surrogate_fallback"] / M
@@ -429,7 +456,7 @@ def run_ours(a, rank, world, local):
         with tempfile.TemporaryDirectory() as td:
             out = os.path.join(td, "s.npz")
             kw = {k: v for k, v in (("n", a.grid), ("n_bodies", a.bodies)) if v is not None}
-            r = run_oracle_sample(a.workload, "exact", [0, nb], 1, out, kw, fast_too=True)
+            r = run_oracle_sample(a.workload, "exact", [0, nb], 1, out, kw, fast_too=True, dt=DT)
             ref = dict(np.load(out))
         fk = torch.as_tensor(ref["fk"], device=dev)
 
@@ -458,6 +485,13 @@ def run_ours(a, rank, world, local):
                          "f": _errs(o["f"], ref["fv"])}
             if mth == "fast":
                 errs[mth]["phi_vs_oracle_fast"] = _errs(o["phi"], ref["phi_fast"])
+        Ts = ctx.transfer(ks)
+        ctx.build_transfer(Ts, xs, as_, "exact")
+        fs = torch.zeros_like(u)
+        Fs, _ = ctx.direct_forcing(Ts, u, torch.zeros((3, ks), dtype=tdt, device=dev), DT, fs)
+        errs["direct_forcing"] = {"F": _errs(Fs.double().cpu().numpy(), ref["F_df"]),
+                                  "f": _errs(fs.reshape(3, -1)[:, fk].double().cpu().numpy(), ref["fv_df"])}
+        Ts.close()
         cpu = {"value": r["markers"] / min(r["times"]), "unit": "markers/s", "cores": 1, "kind": "oracle",
                "sample": f"first {nb} bodies ({r['markers']} markers) of the same workload, prep+exact build"
                          f"+interp+spread, numpy float64, single thread",
