@@ -190,6 +190,27 @@ int mls_spread(mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, void
 int mls_direct_forcing(mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb, double dt,
                        void* U, void* F, void* f, void* stream);
 
+/* Coarse-grained collision detection on the Eulerian mesh (Section 5): a
+ * cell is a collision cell when markers of more than one body have it as
+ * their home cell (the cell of the MLS support built by the last
+ * mls_build_transfer on T).
+ *   body        device, int32[M] body index of each marker (caller order);
+ *               indices start at 1, markers with an index <= 0 take no part
+ *   flag        device, int32[M] output (caller order): 1 when the marker's
+ *               home cell is a collision cell, else 0 (also 0 for dropped
+ *               markers)
+ *   coll        device, int32[nz][ny][nx] or NULL: every cell holding
+ *               participating markers gets the body index when they all
+ *               belong to one body, -1 when they belong to several; other
+ *               cells are not written (the caller zeroes the array, the
+ *               method's initial state)
+ *   n_colliding device, uint64 or NULL: incremented by the number of flagged
+ *               markers
+ * Errors: MLS_ERR_INVALID_ARG on NULL handles, or NULL body or flag with
+ * M > 0. */
+int mls_collisions(mls_ctx* ctx, const mls_transfer* T, const int32_t* body, int32_t* flag, int32_t* coll,
+                   unsigned long long* n_colliding, void* stream);
+
 /* Borrowed device views of the last build (no synchronisation). */
 int mls_transfer_view(const mls_transfer* T, mls_transfer_arrays* out);
 

@@ -167,6 +167,25 @@ class Context:
                                             _stream(stream)), "mls_direct_forcing")
         return F, U
 
+    def collisions(self, T, body, flag=None, coll=None, count=None, stream=None):
+        """Coarse collision flags (mls_collisions): body int32 (M,), returns flag int32 (M,).
+
+        coll (int32 (nz, ny, nx), zeroed by the caller) and count (uint64-sized int64 (1,))
+        are optional outputs."""
+        _check_tensor(body, "body", torch.int32, (T.M,))
+        if flag is None:
+            flag = torch.empty((T.M,), dtype=torch.int32, device=body.device)
+        _check_tensor(flag, "flag", torch.int32, (T.M,))
+        if coll is not None:
+            _check_tensor(coll, "coll", torch.int32, (self.n[2], self.n[1], self.n[0]))
+        if count is not None:
+            _check_tensor(count, "count", torch.int64, (1,))
+        B.check(self.lib.mls_collisions(self.handle, T.handle, _ptr(body), _ptr(flag),
+                                        _ptr(coll) if coll is not None else None,
+                                        _ptr(count) if count is not None else None, _stream(stream)),
+                "mls_collisions")
+        return flag
+
     def status(self, T, stream=None):
         s = B.mls_status()
         rc = self.lib.mls_transfer_status(T.handle, _stream(stream), C.byref(s))

@@ -214,6 +214,7 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
   }
   cudaError_t e = spread_configure(c);
   if (e == cudaSuccess) e = force_configure(c);
+  if (e == cudaSuccess) e = collision_configure(c);
   if (e == cudaSuccess) e = mlp_configure();
   if (e != cudaSuccess) {
     free_ctx(c);
@@ -419,6 +420,19 @@ int mls_direct_forcing(mls_ctx* ctx, const mls_transfer* T, const void* u, const
   cudaError_t e = launch_direct_forcing(ctx, T, u, Vb, dt, U, F, f, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_direct_forcing");
+  return MLS_OK;
+}
+
+int mls_collisions(mls_ctx* ctx, const mls_transfer* T, const int32_t* body, int32_t* flag, int32_t* coll,
+                   unsigned long long* n_colliding, void* stream) {
+  if (!ctx || !T) return invalid("mls_collisions: NULL handle");
+  if (T->ctx != ctx) return invalid("mls_collisions: transfer belongs to another context");
+  if (T->M > 0 && (!body || !flag)) return invalid("mls_collisions: NULL body or flag array");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int slot = timer_begin(ctx, "collisions", s);
+  cudaError_t e = launch_collisions(ctx, T, body, flag, coll, n_colliding, s);
+  timer_end(ctx, slot, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mls_collisions");
   return MLS_OK;
 }
 

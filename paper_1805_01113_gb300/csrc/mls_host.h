@@ -44,6 +44,7 @@ struct mls_ctx {
   int spread_threads;
   int interp_grid;       // persistent grid of the tile-organised interpolation
   int force_grid;        // persistent grid of the fused direct-forcing kernel (0: composed path)
+  int collision_grid;    // persistent grid of the collision detection
   // Learned surrogate: float32 parameters and the packed bfloat16 copy.
   float* mlp_theta;
   unsigned char* mlp_pack;
@@ -106,6 +107,9 @@ cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s);
 cudaError_t launch_direct_forcing(const mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb,
                                   double dt, void* U, void* F, void* f, cudaStream_t s);
 cudaError_t force_configure(mls_ctx* ctx);
+cudaError_t launch_collisions(const mls_ctx* ctx, const mls_transfer* T, const int32_t* body, int32_t* flag,
+                              int32_t* coll, unsigned long long* n_colliding, cudaStream_t s);
+cudaError_t collision_configure(mls_ctx* ctx);
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s);
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s);
 // Surrogate (k_mlp.cu).
