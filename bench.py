@@ -413,6 +413,28 @@ def run_ours(a, rank, world, local):
         "kernel_ms": kd, "algorithmic_bytes_per_launch": bd, "achieved_gbs": bd / (kd / 1e3) / 1e9,
         "frac": bd / (kd / 1e3) / 1e9 / pk["hbm_gbs"],
         "separate_interp_spread_ms": per_launch.get("interp", 0.0) + per_launch.get("spread", 0.0)}
+    # coarse collision detection on the home cells of the exact build (one body index per ellipsoid)
+    step(a.method)
+    bf = np.asarray(w.body_faces)
+    body_t = torch.as_tensor(np.repeat(np.arange(1, len(bf), dtype=np.int32), np.diff(bf)), device=dev)
+    flag_t = torch.empty((M,), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        ctx.collisions(T, body_t, flag_t)
+    torch.cuda.synchronize()
+    ctx.read_timing()
+    ctx.timing(True)
+    for _ in range(5):
+        flush.fill_(1.0)
+        ctx.collisions(T, body_t, flag_t)
+    ctx.collisions(T, body_t, flag_t, count=cnt)
+    torch.cuda.synchronize()
+    kc = ctx.read_timing()["collisions"]
+    ctx.timing(False)
+    kcm = kc[1] / kc[0]
+    others["collisions"] = {"kernel_ms": kcm, "markers_per_s": M * world / (kcm / 1e3),
+                            "colliding_markers": int(cnt.item()),
+                            "step": "mls_collisions on the exact build's home cells, body index per ellipsoid"}
     if "surrogate" in others:
         step("surrogate")
         others["surrogate"]["fallback_rate"] = ctx.status(T)["surrogate_fallback"] / M

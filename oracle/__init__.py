@@ -14,7 +14,7 @@ paper and to mathematics rather than to itself) live in
 ``tests/test_oracle_*.py``; no function here is "parity unpinned".
 """
 
-from . import collision, mlp
+from . import collision, mlp, refine
 from .mls import (
     Grid,
     marker_prep,
@@ -34,7 +34,7 @@ from .mls import (
 )
 
 __all__ = [
-    "collision", "mlp", "Grid", "marker_prep", "locate", "support", "gaussian_weight",
+    "collision", "mlp", "refine", "Grid", "marker_prep", "locate", "support", "gaussian_weight",
     "shape_exact", "shape_exact_absolute_basis", "subnode_offsets", "fast_table",
     "shape_fast", "forcing_scale", "interpolate", "spread", "SparseField",
     "direct_forcing",
