@@ -211,6 +211,36 @@ int mls_direct_forcing(mls_ctx* ctx, const mls_transfer* T, const void* u, const
 int mls_collisions(mls_ctx* ctx, const mls_transfer* T, const int32_t* body, int32_t* flag, int32_t* coll,
                    unsigned long long* n_colliding, void* stream);
 
+/* Adaptive Lagrangian refinement of the forcing markers (Section 3, Fig. 5).
+ * Each base triangle (V1, V2, V3) is split for the forcing step into
+ *   level 0: itself; level 1: (V1, L1, V3), (L1, V2, V3) with L1 = (V1+V2)/2;
+ *   level 2: (V1, V2, L2), (V2, V3, L2), (V3, V1, L2) with L2 the centroid;
+ *   level 3: (V1, L31, L33), (L31, V2, L32), (L33, L32, V3), (L31, L32, L33)
+ *            with L31, L32, L33 the midpoints of V1V2, V2V3, V3V1;
+ * and every refined triangle gives one marker (centroid and area, as
+ * mls_marker_prep).  The level is the smallest k <= max_level for which the
+ * k+1 pieces have l^2 / (k+1) <= (ratio h)^2, where l^2 = 4 A / sqrt(3) is
+ * the squared edge of the equilateral triangle of the same area A and h the
+ * smallest width of the grid cell holding the base centroid (decided in
+ * double precision); a centroid outside the grid keeps level 0.
+ *   vertices device, real[n_vertices][3]   tri device, int32[n_tri][3]
+ *   ratio    target l/h of the refined elements (> 0; 0.8 in the 0.7-0.9
+ *            range the paper recommends)
+ *   max_level 0..3
+ *   x, area  device, real[3][capacity] and real[capacity] outputs (refined
+ *            markers of triangle t are consecutive, triangles in order)
+ *   parent   device, int32[capacity] output: base triangle of each marker
+ *   level    device, int32[n_tri] output, or NULL
+ *   n_markers host, int64 output: the number of refined markers
+ * Synchronizes `stream` (the count is read back).  A triangle with an invalid
+ * vertex index gives one NaN marker (as mls_marker_prep).
+ * Errors: MLS_ERR_CAPACITY when n_markers > capacity (n_markers is still set
+ * and the markers past capacity are not written); MLS_ERR_INVALID_ARG on NULL
+ * pointers, negative sizes, ratio <= 0 or max_level outside 0..3. */
+int mls_refine_markers(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri, int64_t n_tri,
+                       double ratio, int32_t max_level, int64_t capacity, void* x, void* area, int32_t* parent,
+                       int32_t* level, int64_t* n_markers, void* stream);
+
 /* Borrowed device views of the last build (no synchronisation). */
 int mls_transfer_view(const mls_transfer* T, mls_transfer_arrays* out);
 

@@ -56,7 +56,7 @@ def refine_levels(grid, vertices, tri, ratio=0.8, max_level=3, precision="f32"):
     level = np.full(s.shape, max_level, dtype=np.int64)
     for k in range(max_level, -1, -1):
         level = np.where(s <= PIECES[k] * t, k, level)
-    level[~inside] = 0
+    level[~inside | ~np.isfinite(s)] = 0
     return level
 
 

@@ -186,6 +186,24 @@ class Context:
                 "mls_collisions")
         return flag
 
+    def refine_markers(self, vertices, tri, ratio=0.8, max_level=3, capacity=None, stream=None):
+        """Refined forcing markers (mls_refine_markers): returns x (3, K), area (K,), parent (K,), level (n_tri,)."""
+        nt = tri.shape[0]
+        _check_tensor(vertices, "vertices", self.real_t)
+        _check_tensor(tri, "tri", torch.int32, (nt, 3))
+        cap = 4 * nt if capacity is None else int(capacity)
+        dev = vertices.device
+        x = torch.empty((3, cap), dtype=self.real_t, device=dev)
+        area = torch.empty((cap,), dtype=self.real_t, device=dev)
+        parent = torch.empty((cap,), dtype=torch.int32, device=dev)
+        level = torch.empty((nt,), dtype=torch.int32, device=dev)
+        n = C.c_int64()
+        B.check(self.lib.mls_refine_markers(self.handle, _ptr(vertices), vertices.shape[0], _ptr(tri), nt,
+                                            float(ratio), int(max_level), cap, _ptr(x), _ptr(area), _ptr(parent),
+                                            _ptr(level), C.byref(n), _stream(stream)), "mls_refine_markers")
+        K = n.value
+        return x[:, :K].contiguous(), area[:K], parent[:K], level
+
     def status(self, T, stream=None):
         s = B.mls_status()
         rc = self.lib.mls_transfer_status(T.handle, _stream(stream), C.byref(s))

@@ -75,6 +75,9 @@ SIGNATURES = {
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "mls_collisions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p]),
+    "mls_refine_markers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double, C.c_int32,
+                                     C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "mls_transfer_view": (C.c_int, [C.c_void_p, C.POINTER(mls_transfer_arrays)]),
     "mls_transfer_status": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(mls_status)]),
     "mls_fast_table": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),

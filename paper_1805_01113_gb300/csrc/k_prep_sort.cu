@@ -4,24 +4,6 @@
 
 namespace mls {
 
-template <typename R> struct Ops;
-template <> struct Ops<float> {
-  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
-  static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
-  static __device__ __forceinline__ float nan_() { return __int_as_float(0x7fc00000); }
-};
-template <> struct Ops<double> {
-  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
-  static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
-  static __device__ __forceinline__ double nan_() { return __longlong_as_double(0x7ff8000000000000ULL); }
-};
-
 // Centroid C = ((V1+V2)+V3)/3 and area |(V2-V1)x(V3-V1)|/2 of each triangle,
 // every operation rounded to nearest in R with no contraction, so the result
 // is reproducible bit for bit by any IEEE implementation of the same order.
@@ -45,17 +27,11 @@ __global__ void __launch_bounds__(kBlock) k_prep(const R* __restrict__ V, int64_
     b[d] = V[3 * i1 + d];
     c[d] = V[3 * i2 + d];
   }
-  R e1[3], e2[3];
+  R xc[3], ar;
+  triangle_marker(a, b, c, xc, ar);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    x[d * nt + t] = O::div(O::add(O::add(a[d], b[d]), c[d]), R(3));
-    e1[d] = O::sub(b[d], a[d]);
-    e2[d] = O::sub(c[d], a[d]);
-  }
-  const R nx = O::sub(O::mul(e1[1], e2[2]), O::mul(e1[2], e2[1]));
-  const R ny = O::sub(O::mul(e1[2], e2[0]), O::mul(e1[0], e2[2]));
-  const R nz = O::sub(O::mul(e1[0], e2[1]), O::mul(e1[1], e2[0]));
-  area[t] = O::mul(R(0.5), O::sqrt_(O::add(O::add(O::mul(nx, nx), O::mul(ny, ny)), O::mul(nz, nz))));
+  for (int d = 0; d < 3; ++d) x[d * nt + t] = xc[d];
+  area[t] = ar;
 }
 
 cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri, int64_t nt, void* x,

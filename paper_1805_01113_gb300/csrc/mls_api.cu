@@ -124,6 +124,7 @@ static void free_ctx(mls_ctx* c) {
   cudaFree(c->table);
   cudaFree(c->mlp_theta);
   cudaFree(c->mlp_pack);
+  cudaFree(c->refine_ws);
   for (auto& p : c->events) {
     cudaEventDestroy(p.start);
     cudaEventDestroy(p.stop);
@@ -162,6 +163,8 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
   if (!c) return invalid("mls_create: out of host memory");
   c->opt = opt;
   c->table = nullptr;
+  c->refine_ws = nullptr;
+  c->refine_ws_bytes = 0;
   c->n_classes = 0;
   c->class_axis = -1;
   c->timing = 0;
@@ -298,6 +301,42 @@ int mls_marker_prep(mls_ctx* ctx, const void* vertices, int64_t n_vertices, cons
   cudaError_t e = launch_prep(ctx->opt.real, vertices, n_vertices, tri, n_tri, x, area, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_marker_prep");
+  return MLS_OK;
+}
+
+int mls_refine_markers(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri, int64_t n_tri,
+                       double ratio, int32_t max_level, int64_t capacity, void* x, void* area, int32_t* parent,
+                       int32_t* level, int64_t* n_markers, void* stream) {
+  if (!ctx || !n_markers) return invalid("mls_refine_markers: NULL ctx or n_markers");
+  if (n_tri < 0 || n_vertices < 0 || capacity < 0) return invalid("mls_refine_markers: negative size");
+  if (!(ratio > 0.0) || !std::isfinite(ratio)) return invalid("mls_refine_markers: ratio must be positive");
+  if (max_level < 0 || max_level > 3) return invalid("mls_refine_markers: max_level must be in 0..3");
+  if (n_tri > 0 && (!vertices || !tri || !x || !area || !parent))
+    return invalid("mls_refine_markers: NULL pointer");
+  if (n_tri > ((int64_t)1 << 29)) return invalid("mls_refine_markers: too many triangles");
+  *n_markers = 0;
+  if (n_tri == 0) return MLS_OK;
+  const int64_t need = refine_workspace_bytes(n_tri);
+  if (need > ctx->refine_ws_bytes) {
+    cudaFree(ctx->refine_ws);
+    ctx->refine_ws = nullptr;
+    ctx->refine_ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->refine_ws, (size_t)need);
+    if (e != cudaSuccess) return cuda_fail(e, "mls_refine_markers: workspace");
+    ctx->refine_ws_bytes = need;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int slot = timer_begin(ctx, "refine", s);
+  int64_t total = 0;
+  cudaError_t e = launch_refine(ctx, vertices, n_vertices, tri, n_tri, ratio, max_level, capacity, x, area, parent,
+                                level, ctx->refine_ws, &total, s);
+  timer_end(ctx, slot, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mls_refine_markers");
+  *n_markers = total;
+  if (total > capacity) {
+    set_error("mls_refine_markers: more refined markers than capacity");
+    return MLS_ERR_CAPACITY;
+  }
   return MLS_OK;
 }
 

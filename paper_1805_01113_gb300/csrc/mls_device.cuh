@@ -11,6 +11,44 @@ namespace mls {
 
 // One grid axis.  Cell i spans [faces[i], faces[i+1]); `uniform` axes also
 // carry lo and h so the home cell comes from one multiply plus a face check.
+// IEEE operations rounded to nearest with no contraction, so that a fixed
+// order of operations is reproducible bit for bit by any IEEE implementation.
+template <typename R> struct Ops;
+template <> struct Ops<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float nan_() { return __int_as_float(0x7fc00000); }
+};
+template <> struct Ops<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double nan_() { return __longlong_as_double(0x7ff8000000000000ULL); }
+};
+
+// Marker of a triangle (Section 3): centroid C = ((V1+V2)+V3)/3 and area
+// |(V2-V1)x(V3-V1)|/2, in this order of operations.
+template <typename R>
+__device__ __forceinline__ void triangle_marker(const R a[3], const R b[3], const R c[3], R x[3], R& area) {
+  using O = Ops<R>;
+  R e1[3], e2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    x[d] = O::div(O::add(O::add(a[d], b[d]), c[d]), R(3));
+    e1[d] = O::sub(b[d], a[d]);
+    e2[d] = O::sub(c[d], a[d]);
+  }
+  const R nx = O::sub(O::mul(e1[1], e2[2]), O::mul(e1[2], e2[1]));
+  const R ny = O::sub(O::mul(e1[2], e2[0]), O::mul(e1[0], e2[2]));
+  const R nz = O::sub(O::mul(e1[0], e2[1]), O::mul(e1[1], e2[0]));
+  area = O::mul(R(0.5), O::sqrt_(O::add(O::add(O::mul(nx, nx), O::mul(ny, ny)), O::mul(nz, nz))));
+}
+
 template <typename R>
 struct Axis {
   const R* faces;   // n+1 values (device)
