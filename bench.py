@@ -435,6 +435,46 @@ def run_ours(a, rank, world, local):
     others["collisions"] = {"kernel_ms": kcm, "markers_per_s": M * world / (kcm / 1e3),
                             "colliding_markers": int(cnt.item()),
                             "step": "mls_collisions on the exact build's home cells, body index per ellipsoid"}
+    # adaptive Lagrangian refinement of the same bodies (target element 0.8 h), then
+    # the transfer step on the refined markers
+    tri_t = tri
+    for _ in range(2):
+        xr, ar, pr, lv = ctx.refine_markers(V, tri_t, ratio=0.8)
+    ctx.read_timing()
+    ctx.timing(True)
+    for _ in range(3):
+        flush.fill_(1.0)
+        xr, ar, pr, lv = ctx.refine_markers(V, tri_t, ratio=0.8)
+    kr = ctx.read_timing()["refine"]
+    ctx.timing(False)
+    Kr = xr.shape[1]
+    Tr = ctx.transfer(Kr)
+    Fr = torch.randn((3, Kr), dtype=tdt, device=dev)
+    Ur = torch.empty((3, Kr), dtype=tdt, device=dev)
+
+    def refined_step():
+        ctx.build_transfer(Tr, xr, ar, "exact")
+        ctx.interpolate(Tr, u, Ur)
+        ctx.spread(Tr, Fr, f)
+
+    for _ in range(3):
+        refined_step()
+    torch.cuda.synchronize()
+    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for e0, e1 in evr:
+        flush.fill_(1.0)
+        e0.record(stream)
+        refined_step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    msr = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evr)
+    others["refinement"] = {"base_markers": M, "refined_markers": Kr,
+                            "levels": torch.bincount(lv.long(), minlength=4).tolist(),
+                            "refine_ms": kr[1] / kr[0], "transfer_ms": msr,
+                            "refined_markers_per_s": Kr * world / (msr / 1e3),
+                            "step": "mls_refine_markers (ratio 0.8, max level 3) timed alone; build (exact) + "
+                                    "interp + spread on the refined markers"}
+    Tr.close()
     if "surrogate" in others:
         step("surrogate")
         others["surrogate"]["fallback_rate"] = ctx.status(T)["surrogate_fallback"] / M

@@ -23,6 +23,8 @@ from .mls import (
     gaussian_weight,
     shape_exact,
     shape_exact_absolute_basis,
+    shape_exact_gradient,
+    interpolate_gradient,
     subnode_offsets,
     fast_table,
     shape_fast,
@@ -35,7 +37,7 @@ from .mls import (
 
 __all__ = [
     "collision", "mlp", "refine", "Grid", "marker_prep", "locate", "support", "gaussian_weight",
-    "shape_exact", "shape_exact_absolute_basis", "subnode_offsets", "fast_table",
+    "shape_exact", "shape_exact_absolute_basis", "shape_exact_gradient", "interpolate_gradient", "subnode_offsets", "fast_table",
     "shape_fast", "forcing_scale", "interpolate", "spread", "SparseField",
     "direct_forcing",
 ]

@@ -192,6 +192,63 @@ def shape_exact(grid, x, eps=1.0, home=None):
     return Transfer(phi, sup)
 
 
+def shape_exact_gradient(grid, x, eps=1.0, home=None):
+    """Spatial derivatives of the exact-MLS shape functions at the markers.
+
+    The paper uses MLS also for velocity and pressure gradients at the marker
+    (Section 2: derivatives of the interpolated field); the derivative of
+    Eq. 6 with respect to the evaluation point x follows from the product
+    rule.  With the basis centred at a fixed c = x_l,
+    p~(y) = [1, (y - c)/Delta^home], A(x) = sum_j W_j(x) p~_j p~_j^T (Eq. 3)
+    and gamma = A^-1 p~(x):
+        d_d phi_k = d_d W_k p~_k^T gamma + W_k p~_k^T A^-1 (d_d p~ - d_d A gamma),
+    d_d A = sum_j d_d W_j p~_j p~_j^T, d_d p~ = e_{d+1}/Delta_d, and for the
+    Gaussian d_d W_j = W_j 2 (x_j,d - x_d) / (eps Delta_d)^2.  The home cell
+    (and so the support and the width scaling) is held fixed.
+
+    Returns dphi (M, 3, 27), zero rows for unusable markers.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    sup = support(grid, x, home)
+    W = gaussian_weight(x, sup, eps)                       # (M, 27)
+    M = x.shape[1]
+    P = np.ones((M, 27, 4))
+    for d in range(3):
+        P[:, :, d + 1] = (sup.pos[d] - x[d][:, None]) / sup.hwidth[d][:, None]
+    A = np.einsum("mk,mki,mkj->mij", W, P, P)
+    dphi = np.zeros((M, 3, 27))
+    good = sup.ok
+    if not np.any(good):
+        return dphi
+    Ag, Wg, Pg = A[good], W[good], P[good]
+    pl = np.zeros((Ag.shape[0], 4))
+    pl[:, 0] = 1.0
+    gamma = np.linalg.solve(Ag, pl[:, :, None])[:, :, 0]   # A^-1 p~(x_l)
+    out = np.zeros((Ag.shape[0], 3, 27))
+    for d in range(3):
+        hd = sup.hwidth[d][good][:, None]
+        dW = Wg * 2.0 * (sup.pos[d][good] - x[d][good][:, None]) / (eps * hd) ** 2
+        dA = np.einsum("mk,mki,mkj->mij", dW, Pg, Pg)
+        dp = np.zeros((Ag.shape[0], 4))
+        dp[:, d + 1] = 1.0 / hd[:, 0]
+        rhs = dp - np.einsum("mij,mj->mi", dA, gamma)
+        dgamma = np.linalg.solve(Ag, rhs[:, :, None])[:, :, 0]
+        out[:, d] = dW * np.einsum("mki,mi->mk", Pg, gamma) + Wg * np.einsum("mki,mi->mk", Pg, dgamma)
+    dphi[good] = out
+    return dphi
+
+
+def interpolate_gradient(dphi, sup, u):
+    """Velocity gradient at the markers: G[c, d, l] = sum_k d_d phi_k^l u_c,k."""
+    ix, iy, iz = sup.idx
+    G = np.empty((3, 3, dphi.shape[0]))
+    for c in range(3):
+        uk = u[c][iz, iy, ix]                              # (M, 27)
+        for d in range(3):
+            G[c, d] = np.sum(dphi[:, d] * uk, axis=1)
+    return G
+
+
 def shape_exact_absolute_basis(grid, x, eps=1.0, home=None):
     """Eqs. 3, 4, 6 exactly as printed, with p = [1, x, y, z] in absolute coordinates.
 
