@@ -165,6 +165,22 @@ int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void*
  * Dropped markers get U = 0. */
 int mls_interpolate(mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, void* stream);
 
+/* Gradients of an interpolated field at the markers (Section 2: MLS also
+ * approximates spatial derivatives, which the solver needs for velocity and
+ * pressure gradients at the markers): G[c][d][l] = sum_k d_d phi_k^l u_c,k,
+ * with d_d phi the derivative of the exact-MLS shape functions (Eq. 6) with
+ * respect to the marker position, the support and home cell of the last
+ * build of T held fixed.  With gamma = A^-1 p(x_l):
+ *   d_d phi_k = d_d W_k p_k.gamma + W_k p_k.A^-1 (d_d p - d_d A gamma).
+ * The shape-function derivatives are formed on the fly (not stored), for
+ * every method T was built with.
+ *   x  device, real[3][M] the marker positions given to mls_build_transfer
+ *   u  device, field[3][nz][ny][nx]      G  device, real[3][3][M] (component,
+ *      direction, caller's marker order)
+ * Dropped markers get G = 0. */
+int mls_interpolate_gradient(mls_ctx* ctx, const mls_transfer* T, const void* x, const void* u, void* G,
+                             void* stream);
+
 /* Lagrange-to-Euler spreading f_k += sum_l c_l phi_k^l F_l (text after
  * Eq. 7).  Accumulates into f (the caller zeroes it when it wants a fresh
  * field); partial sums are formed per spreading tile in the real type and

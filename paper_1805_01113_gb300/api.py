@@ -146,6 +146,17 @@ class Context:
                 "mls_interpolate")
         return U
 
+    def interpolate_gradient(self, T, x, u, G=None, stream=None):
+        """G[c, d, l] = d u_c / d x_d at marker l from the exact-MLS shape-function derivatives."""
+        _check_tensor(x, "x", self.real_t, (3, T.M))
+        _check_tensor(u, "u", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        if G is None:
+            G = torch.empty((3, 3, T.M), dtype=self.real_t, device=u.device)
+        _check_tensor(G, "G", self.real_t, (3, 3, T.M))
+        B.check(self.lib.mls_interpolate_gradient(self.handle, T.handle, _ptr(x), _ptr(u), _ptr(G), _stream(stream)),
+                "mls_interpolate_gradient")
+        return G
+
     def spread(self, T, F, f, stream=None):
         _check_tensor(F, "F", self.real_t, (3, T.M))
         _check_tensor(f, "f", self.field_t, (3, self.n[2], self.n[1], self.n[0]))

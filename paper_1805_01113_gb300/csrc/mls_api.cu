@@ -436,6 +436,19 @@ int mls_interpolate(mls_ctx* ctx, const mls_transfer* T, const void* u, void* U,
   return MLS_OK;
 }
 
+int mls_interpolate_gradient(mls_ctx* ctx, const mls_transfer* T, const void* x, const void* u, void* G,
+                             void* stream) {
+  if (!ctx || !T) return invalid("mls_interpolate_gradient: NULL handle");
+  if (T->ctx != ctx) return invalid("mls_interpolate_gradient: transfer belongs to another context");
+  if (T->M > 0 && (!x || !u || !G)) return invalid("mls_interpolate_gradient: NULL positions, field or output");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int slot = timer_begin(ctx, "interp_gradient", s);
+  cudaError_t e = launch_interp_gradient(ctx, T, x, u, G, s);
+  timer_end(ctx, slot, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mls_interpolate_gradient");
+  return MLS_OK;
+}
+
 int mls_spread(mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, void* stream) {
   if (!ctx || !T) return invalid("mls_spread: NULL handle");
   if (T->ctx != ctx) return invalid("mls_spread: transfer belongs to another context");

@@ -116,6 +116,8 @@ int64_t refine_workspace_bytes(int64_t nt);
 cudaError_t launch_refine(const mls_ctx* ctx, const void* V, int64_t nv, const int32_t* tri, int64_t nt,
                           double ratio, int max_level, int64_t capacity, void* x, void* area, int32_t* parent,
                           int32_t* level, void* ws, int64_t* total_host, cudaStream_t s);
+cudaError_t launch_interp_gradient(const mls_ctx* ctx, const mls_transfer* T, const void* x, const void* u, void* G,
+                                   cudaStream_t s);
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s);
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s);
 // Surrogate (k_mlp.cu).
