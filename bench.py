@@ -133,6 +133,10 @@ for rep in range(args["reps"]):
     sp = oracle.spread(tr, c, F, g.n)
     times.append(time.perf_counter() - t0)
 out = {"phi": tr.phi, "U": U, "c": c, "fk": sp.keys, "fv": sp.values}
+if args.get("grad"):
+    # velocity gradient at the markers (exact-MLS shape-function derivatives)
+    dphi = oracle.shape_exact_gradient(g, x, 1.0)
+    out["G"] = np.einsum("mdk,cmk->cdm", dphi, usup)
 if args.get("dt"):
     # direct forcing with V_b = 0 (bodies at rest): F = (V_b - U)/dt, spread on the same support
     F_df = (0.0 - U) / args["dt"]
@@ -145,13 +149,13 @@ print(json.dumps({"markers": int(f1 - f0), "times": times}))
 """
 
 
-def run_oracle_sample(name, method, bodies, reps, out, kw=None, fast_too=False, dt=None):
+def run_oracle_sample(name, method, bodies, reps, out, kw=None, fast_too=False, dt=None, grad=False):
     env = dict(os.environ)
     env["MLS_ROOT"] = ROOT
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     args = json.dumps({"workload": name, "method": method, "bodies": bodies, "reps": reps, "out": out,
-                       "kw": kw or {}, "fast_too": fast_too, "dt": dt})
+                       "kw": kw or {}, "fast_too": fast_too, "dt": dt, "grad": grad})
     r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, args], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
@@ -413,6 +417,27 @@ def run_ours(a, rank, world, local):
         "kernel_ms": kd, "algorithmic_bytes_per_launch": bd, "achieved_gbs": bd / (kd / 1e3) / 1e9,
         "frac": bd / (kd / 1e3) / 1e9 / pk["hbm_gbs"],
         "separate_interp_spread_ms": per_launch.get("interp", 0.0) + per_launch.get("spread", 0.0)}
+    # velocity gradient at the markers from the exact-MLS shape-function derivatives
+    step(a.method)
+    Gt = torch.empty((3, 3, M), dtype=tdt, device=dev)
+    for _ in range(3):
+        ctx.interpolate_gradient(T, x, u, Gt)
+    torch.cuda.synchronize()
+    ctx.read_timing()
+    ctx.timing(True)
+    for _ in range(5):
+        flush.fill_(1.0)
+        ctx.interpolate_gradient(T, x, u, Gt)
+    torch.cuda.synchronize()
+    kg = ctx.read_timing()["interp_gradient"]
+    ctx.timing(False)
+    kgm = kg[1] / kg[0]
+    # x, home, perm, 27 gathered u cells x 3 components (touched cells), G out
+    bg = (3 * rs + 8 + 3 * rs * u_cells + 9 * rs) * M
+    others["interp_gradient"] = {"kernel_ms": kgm, "markers_per_s": M * world / (kgm / 1e3),
+                                 "algorithmic_bytes_per_launch": bg, "achieved_gbs": bg / (kgm / 1e3) / 1e9,
+                                 "step": "mls_interpolate_gradient on the exact build (9 gradient components)"}
+
     # coarse collision detection on the home cells of the exact build (one body index per ellipsoid)
     step(a.method)
     bf = np.asarray(w.body_faces)
@@ -518,7 +543,7 @@ def run_ours(a, rank, world, local):
         with tempfile.TemporaryDirectory() as td:
             out = os.path.join(td, "s.npz")
             kw = {k: v for k, v in (("n", a.grid), ("n_bodies", a.bodies)) if v is not None}
-            r = run_oracle_sample(a.workload, "exact", [0, nb], 1, out, kw, fast_too=True, dt=DT)
+            r = run_oracle_sample(a.workload, "exact", [0, nb], 1, out, kw, fast_too=True, dt=DT, grad=True)
             ref = dict(np.load(out))
         fk = torch.as_tensor(ref["fk"], device=dev)
 
@@ -550,9 +575,11 @@ def run_ours(a, rank, world, local):
         Ts = ctx.transfer(ks)
         ctx.build_transfer(Ts, xs, as_, "exact")
         fs = torch.zeros_like(u)
-        Fs, _ = ctx.direct_forcing(Ts, u, torch.zeros((3, ks), dtype=tdt, device=dev), DT, fs)
-        errs["direct_forcing"] = {"F": _errs(Fs.double().cpu().numpy(), ref["F_df"]),
+        F_dfs, _ = ctx.direct_forcing(Ts, u, torch.zeros((3, ks), dtype=tdt, device=dev), DT, fs)
+        errs["direct_forcing"] = {"F": _errs(F_dfs.double().cpu().numpy(), ref["F_df"]),
                                   "f": _errs(fs.reshape(3, -1)[:, fk].double().cpu().numpy(), ref["fv_df"])}
+        Gs = ctx.interpolate_gradient(Ts, xs, u)
+        errs["interp_gradient"] = {"G": _errs(Gs.double().cpu().numpy(), ref["G"])}
         Ts.close()
         cpu = {"value": r["markers"] / min(r["times"]), "unit": "markers/s", "cores": 1, "kind": "oracle",
                "sample": f"first {nb} bodies ({r['markers']} markers) of the same workload, prep+exact build"
