@@ -265,8 +265,12 @@ int mls_transfer_view(const mls_transfer* T, mls_transfer_arrays* out);
 int mls_transfer_status(const mls_transfer* T, void* stream, mls_status* out);
 
 /* Fast-MLS table of the context (built on demand on `stream`):
- * real[n_classes][n_sub^3][27], sub-node order s = (s_z*n + s_y)*n + s_x,
- * class = home index along the one non-uniform axis (0 when all are uniform). */
+ * real[n_classes][n_sub^3][MLS_TABLE_ROW], sub-node order
+ * s = (s_z*n + s_y)*n + s_x, class = home index along the one non-uniform
+ * axis (0 when all are uniform); a row holds the 27 exact shape-function
+ * values of the sub-node (k = 9 c + 3 b + a) and one zero pad, so rows are
+ * 16-byte aligned. */
+#define MLS_TABLE_ROW 28
 int mls_fast_table(mls_ctx* ctx, void* stream, const void** table, int64_t* n_classes, int32_t* n_sub);
 
 /* Build without allocating.  The paper has no counterpart: this is a

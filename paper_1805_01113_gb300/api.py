@@ -242,7 +242,10 @@ class Context:
                 "mls_fast_table")
         s3 = ns.value ** 3
         dev = torch.device("cuda", torch.cuda.current_device())
-        return torch.as_tensor(_DeviceArray(p.value, (nc.value, s3, 27), self.real_t), device=dev)
+        es = torch.empty((), dtype=self.real_t).element_size()
+        row = B.MLS_TABLE_ROW
+        return torch.as_tensor(_DeviceArray(p.value, (nc.value, s3, 27), self.real_t,
+                                            (s3 * row * es, row * es, es)), device=dev)
 
     # -- learned surrogate ----------------------------------------------------
     def train_surrogate(self, stream=None, **kw):

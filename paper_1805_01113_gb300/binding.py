@@ -20,6 +20,7 @@ MLS_EXACT = 0
 MLS_FAST = 1
 MLS_SURROGATE = 2
 MLS_MLP_PARAMS = 6363
+MLS_TABLE_ROW = 28
 
 MLS_F64 = 0
 MLS_F32 = 1

@@ -8,6 +8,10 @@
 
 namespace mls {
 
+template <typename R> struct TableVec;
+template <> struct TableVec<float> { using type = float4; };
+template <> struct TableVec<double> { using type = double2; };
+
 template <typename R>
 struct BuildArgs {
   Grid<R> g;
@@ -173,29 +177,40 @@ __global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
   }
   const R inv = R(1) / sum;
   const int cl = a.class_axis >= 0 ? h[a.class_axis] : 0;
-  const R* T = a.table + (int64_t)cl * n * n * n * 27 +
-               (int64_t)(((sc[2] * n) + sc[1]) * n + sc[0]) * 27;
+  const R* T = a.table + ((int64_t)cl * n * n * n + (int64_t)(((sc[2] * n) + sc[1]) * n + sc[0])) * kTableRow;
   // Corner q sits at sub-node offset (q&1, (q>>1)&1, q>>2) from the sub-cell origin.
   int64_t roff[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     alpha[q] *= inv;
-    roff[q] = (int64_t)((((q >> 2) * n) + ((q >> 1) & 1)) * n + (q & 1)) * 27;
+    roff[q] = (int64_t)((((q >> 2) * n) + ((q >> 1) & 1)) * n + (q & 1)) * kTableRow;
   }
+  // Rows are kTableRow = 28 values (27 + one pad), 16-byte aligned: read in
+  // 16-byte vectors, kTableRow / kVec of them per corner.
+  using V = typename TableVec<R>::type;
+  constexpr int kVec = 16 / sizeof(R);
   ScaleSums<R> sums;
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int v = 0; v < kTableRow / kVec; ++v) {
+    R acc[kVec];
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+    for (int e = 0; e < kVec; ++e) acc[e] = R(0);
 #pragma unroll
-      for (int q3 = 0; q3 < 3; ++q3) {
-        const int k = 9 * c + 3 * b + q3;
-        R v = R(0);
+    for (int q = 0; q < 8; ++q) {
+      const V t = __ldg(reinterpret_cast<const V*>(T + roff[q]) + v);
+      const R* tv = reinterpret_cast<const R*>(&t);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v += alpha[q] * __ldg(T + roff[q] + k);
-        a.phi[k * a.cap + j] = v;
-        sums.add(s, q3, b, c, v);
+      for (int e = 0; e < kVec; ++e) acc[e] += alpha[q] * tv[e];
+    }
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) {
+      const int k = v * kVec + e;
+      if (k < 27) {
+        a.phi[k * a.cap + j] = acc[e];
+        sums.add(s, k % 3, (k / 3) % 3, k / 9, acc[e]);
       }
+    }
+  }
   marker_finish(a, j, h, s, sums, ar);
 }
 
@@ -230,7 +245,8 @@ __global__ void k_fast_table(Grid<double> gd, int class_axis, int64_t n_classes,
   if (!shape_exact<double>(nd, inv_eps2, 0, phi, nullptr)) {
     for (int k = 0; k < 27; ++k) phi[k] = 0.0;
   }
-  for (int k = 0; k < 27; ++k) table[idx * 27 + k] = (R)phi[k];
+  for (int k = 0; k < 27; ++k) table[idx * kTableRow + k] = (R)phi[k];
+  for (int k = 27; k < kTableRow; ++k) table[idx * kTableRow + k] = R(0);
 }
 
 template <typename R>

@@ -356,7 +356,7 @@ static int ensure_table(mls_ctx* ctx, cudaStream_t s) {
   ctx->n_classes = axis < 0 ? 1 : ctx->n[axis];
   const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
   const size_t rs = ctx->opt.real == MLS_F64 ? sizeof(double) : sizeof(float);
-  cudaError_t e = cudaMalloc(&ctx->table, (size_t)ctx->n_classes * S3 * 27 * rs);
+  cudaError_t e = cudaMalloc(&ctx->table, (size_t)ctx->n_classes * S3 * kTableRow * rs);
   if (e != cudaSuccess) {
     ctx->table = nullptr;
     return cuda_fail(e, "fast-MLS table allocation");
