@@ -160,6 +160,47 @@ __device__ __forceinline__ void block_max3(float v[3], float* red) {
 // integer in the low mantissa bits.
 __device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
 
+// Adds one marker's 27 x 3 fixed-point terms round(phi_k q_c) into the shared
+// accumulator, a0 pointing at the stencil's (-1,-1,-1) cell, rows AX cells
+// apart, planes PS, components ACC.  Markers of one warp often share a home
+// cell (tile order follows the caller's surface order), and lanes that add to
+// one word in the same instruction are serialised.  So each lane walks the
+// stencil in its own order: x rotated by lane % 3 and z by (lane / 3) % 3;
+// at step (cz, cy, cx) the lane adds node ((cz + rc) % 3, cy, (cx + ra) % 3).
+// The integer sums do not depend on the order.
+__device__ __forceinline__ void add_stencil_fixed(int* a0, const float p[27], float q0, float q1, float q2, int PS,
+                                                  int AX, int ACC) {
+  const int lane = threadIdx.x & 31;
+  const int ra = lane % 3, rc = (lane / 3) % 3;
+  float t[27];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const float v0 = p[3 * r], v1 = p[3 * r + 1], v2 = p[3 * r + 2];
+    t[3 * r] = ra == 0 ? v0 : (ra == 1 ? v1 : v2);
+    t[3 * r + 1] = ra == 0 ? v1 : (ra == 1 ? v2 : v0);
+    t[3 * r + 2] = ra == 0 ? v2 : (ra == 1 ? v0 : v1);
+  }
+  const int xo[3] = {ra, ra == 2 ? 0 : ra + 1, ra == 0 ? 2 : ra - 1};
+  const int zo[3] = {rc * PS, (rc == 2 ? 0 : rc + 1) * PS, (rc == 0 ? 2 : rc - 1) * PS};
+#pragma unroll
+  for (int cz = 0; cz < 3; ++cz) {
+    const int z1 = (cz + 1) % 3, z2 = (cz + 2) % 3;
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+      int* ar = a0 + zo[cz] + cy * AX;
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) {
+        const int m = 3 * cy + cx;
+        const float pk = rc == 0 ? t[9 * cz + m] : (rc == 1 ? t[9 * z1 + m] : t[9 * z2 + m]);
+        int* a = ar + xo[cx];
+        atomicAdd(a, round_small(pk * q0));
+        atomicAdd(a + ACC, round_small(pk * q1));
+        atomicAdd(a + 2 * ACC, round_small(pk * q2));
+      }
+    }
+  }
+}
+
 inline Dims dims_of(const mls_ctx* ctx) {
   Dims D;
   for (int d = 0; d < 3; ++d) {
