@@ -225,7 +225,7 @@ class ClockSampler:
 
 def traffic_for(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary of this kernel on this
-    workload (default sizes), if the kernel's source is unchanged since the capture."""
+    workload (default sizes), if the kernel's sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(p))
@@ -234,12 +234,21 @@ def traffic_for(kernel, workload):
     ent = data.get(kernel, {}).get(workload)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_1805_01113_gb300", "csrc", ent["source"])
+    h = source_sha(ent["source"])
+    return ent["bytes_per_launch"] if h is not None and h == ent["source_sha"] else None
+
+
+def source_sha(files):
+    """sha256 (16 hex digits) of the named csrc files, concatenated in the order given."""
+    if isinstance(files, str):
+        files = [files]
+    d = hashlib.sha256()
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for name in files:
+            d.update(open(os.path.join(ROOT, "paper_1805_01113_gb300", "csrc", name), "rb").read())
     except OSError:
         return None
-    return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+    return d.hexdigest()[:16]
 
 
 def peaks():

@@ -170,20 +170,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
 #pragma unroll
         for (int k = 0; k < 27; ++k) pmax = fmaxf(pmax, fabsf(p[k]));
         if (pmax <= 0.5f) {
-          int* a0 = acc + base;
-#pragma unroll
-          for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-            for (int cy = 0; cy < 3; ++cy) {
-              int* ar = a0 + cz * PS + cy * AX;
-#pragma unroll
-              for (int cx = 0; cx < 3; ++cx) {
-                const float pk = p[9 * cz + 3 * cy + cx];
-                atomicAdd(ar + cx, round_small(pk * q0));
-                atomicAdd(ar + ACC + cx, round_small(pk * q1));
-                atomicAdd(ar + 2 * ACC + cx, round_small(pk * q2));
-              }
-            }
+          add_stencil_fixed(acc + base, p, q0, q1, q2, PS, AX, ACC);
         } else {
 #pragma unroll
           for (int k = 0; k < 27; ++k) {
