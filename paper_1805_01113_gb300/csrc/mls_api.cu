@@ -42,6 +42,7 @@ Grid<R> device_grid(const mls_ctx* ctx) {
     a.lo = (R)f.front();
     a.hi = (R)f.back();
     a.h = (R)(f[1] - f[0]);
+    a.inv_h = (R)(1.0 / (f[1] - f[0]));
   }
   return g;
 }

@@ -54,6 +54,7 @@ struct Axis {
   const R* faces;   // n+1 values (device)
   const R* widths;  // n values (device)
   R lo, hi, h;      // faces[0], faces[n], width when uniform
+  R inv_h;          // 1/h when uniform (rounded)
   int n;
   int periodic;
   int uniform;
@@ -74,14 +75,14 @@ struct Tiles {
 
 // Home cell of coordinate x on one axis: face_i <= x < face_{i+1}.  Returns -1
 // outside [faces[0], faces[n]) or for NaN.  Uniform axes guess i from
-// (x - lo)/h and correct it against the face array, so the result agrees with
-// the exact comparison whatever the rounding of the guess.
+// (x - lo) * (1/h) and correct it against the face array, so the result agrees
+// with the exact comparison whatever the rounding of the guess.
 template <typename R>
 __device__ __forceinline__ int locate_axis(const Axis<R>& a, R x) {
   if (!(x >= a.lo && x < a.hi)) return -1;
   int i;
   if (a.uniform) {
-    R s = (x - a.lo) / a.h;
+    R s = (x - a.lo) * a.inv_h;
     i = (int)s;
     i = i < 0 ? 0 : (i > a.n - 1 ? a.n - 1 : i);
     if (x < a.faces[i]) --i;
@@ -126,9 +127,20 @@ struct AxisNodes {
   R t;
 };
 
+// On a uniform axis both width ratios are exactly 1 and the offset is
+// (x - face_i) * (1/h), which equals (x - face_i)/h when h is a power of two.
 template <typename R>
 __device__ __forceinline__ AxisNodes<R> axis_nodes(const Axis<R>& a, int i, R x) {
   AxisNodes<R> s;
+  if (a.uniform) {
+    s.frac = (x - a.faces[i]) * a.inv_h;
+    s.t = s.frac - R(0.5);
+    s.xi[0] = R(-1) - s.t;
+    s.xi[1] = -s.t;
+    s.xi[2] = R(1) - s.t;
+    s.w[0] = s.w[1] = s.w[2] = a.h;
+    return s;
+  }
   const R wh = width_of(a, i);
   const R wm = width_of(a, wrap(i - 1, a.n, a.periodic));
   const R wp = width_of(a, wrap(i + 1, a.n, a.periodic));
@@ -160,7 +172,15 @@ __device__ __forceinline__ AxisNodes<R> axis_nodes_at(R t, R wm, R wh, R wp) {
 }
 
 template <typename R> __device__ __forceinline__ R dev_exp(R v);
-template <> __device__ __forceinline__ float dev_exp<float>(float v) { return expf(v); }
+// Single precision takes the hardware exponential: for the arguments here
+// (|v| <= 4 with eps = 1) its relative error is a few ulp, far inside the
+// single-precision tolerance of the shape functions.
+template <> __device__ __forceinline__ float dev_exp<float>(float v) { return __expf(v); }
+
+// 1/sqrt(d): the hardware reciprocal square root in single precision (about
+// 1 ulp; the solve is followed by a refinement step), IEEE operations in double.
+__device__ __forceinline__ float inv_sqrt(float d) { return rsqrtf(d); }
+__device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
 template <> __device__ __forceinline__ double dev_exp<double>(double v) { return exp(v); }
 
 // 4x4 symmetric positive definite solve by Cholesky, A packed lower-triangular
@@ -174,23 +194,22 @@ struct Chol4 {
   __device__ __forceinline__ void factor(const R a[10]) {
     R d0 = a[0];
     ok = d0 > R(0);
-    R l00 = sqrt(d0);
-    i0 = R(1) / l00;
+    i0 = inv_sqrt(d0);
     l10 = a[1] * i0;
     l20 = a[3] * i0;
     l30 = a[6] * i0;
     R d1 = a[2] - l10 * l10;
     ok = ok && d1 > R(0);
-    i1 = R(1) / sqrt(d1);
+    i1 = inv_sqrt(d1);
     l21 = (a[4] - l20 * l10) * i1;
     l31 = (a[7] - l30 * l10) * i1;
     R d2 = a[5] - l20 * l20 - l21 * l21;
     ok = ok && d2 > R(0);
-    i2 = R(1) / sqrt(d2);
+    i2 = inv_sqrt(d2);
     l32 = (a[8] - l30 * l20 - l31 * l21) * i2;
     R d3 = a[9] - l30 * l30 - l31 * l31 - l32 * l32;
     ok = ok && d3 > R(0);
-    i3 = R(1) / sqrt(d3);
+    i3 = inv_sqrt(d3);
   }
 
   __device__ __forceinline__ void solve(const R b[4], R y[4]) const {
