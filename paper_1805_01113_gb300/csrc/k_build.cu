@@ -3,6 +3,8 @@
 // One thread per marker, markers visited in tile order (perm), so phi[k][j],
 // c[j] and home[j] are written with unit stride across a warp.
 #include <algorithm>
+#include <cmath>
+#include <limits>
 
 #include "mls_host.h"
 
@@ -28,7 +30,8 @@ struct BuildArgs {
   R inv_eps2;
   double inv_eps2_d;
   int refine;
-  double cond_max;
+  int want_cond;         // single precision with cond_max > 0
+  float cond_max_f;      // cond_max rounded down to float: cond > cond_max_f <=> cond > cond_max
   // fast-MLS
   const R* table;
   int class_axis;
@@ -83,23 +86,22 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact(
   if (!marker_setup(a, j, h, p, s, ar)) return;
   R w[3][3], y[4];
   R cond = R(0);
-  const bool want_cond = sizeof(R) == 4 && a.cond_max > 0.0;
+  const bool want_cond = sizeof(R) == 4 && a.want_cond;
   bool good = exact_solve<R>(s, a.inv_eps2, a.refine, w, y, want_cond ? &cond : nullptr);
-  if (sizeof(R) == 4 && (!good || (want_cond && (double)cond > a.cond_max))) {
+  if (sizeof(R) == 4 && (!good || (want_cond && (float)cond > a.cond_max_f))) {
     a.redo[atomicAdd(&a.status[2], 1ULL)] = (int32_t)j;
     return;
   }
-  ScaleSums<R> sums;
+  R c = R(0);
   if (good) {
-    exact_emit(s, w, y, [&](int q, int b, int c, R v) {
-      a.phi[(9 * c + 3 * b + q) * a.cap + j] = v;
-      sums.add(s, q, b, c, v);
-    });
+    c = exact_scale(s, w, y, ar);
+    exact_emit(s, w, y, [&](int q, int b, int cc, R v) { a.phi[(9 * cc + 3 * b + q) * a.cap + j] = v; });
   } else {
 #pragma unroll
     for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = R(0);
   }
-  marker_finish(a, j, h, s, sums, ar);
+  a.c[j] = c;
+  a.home[j] = (h[2] * a.g.ax[1].n + h[1]) * a.g.ax[0].n + h[0];
 }
 
 // The queued single-precision markers, solved in double and rounded
@@ -267,7 +269,10 @@ static BuildArgs<R> make_args(const mls_ctx* ctx, mls_transfer* T, const void* x
   a.inv_eps2 = (R)(1.0 / (ctx->opt.eps * ctx->opt.eps));
   a.inv_eps2_d = 1.0 / (ctx->opt.eps * ctx->opt.eps);
   a.refine = ctx->opt.real == MLS_F32 ? ctx->opt.refine : 0;
-  a.cond_max = ctx->opt.cond_max;
+  a.want_cond = ctx->opt.real == MLS_F32 && ctx->opt.cond_max > 0.0;
+  float t = (float)ctx->opt.cond_max;
+  if ((double)t > ctx->opt.cond_max) t = std::nextafter(t, -std::numeric_limits<float>::infinity());
+  a.cond_max_f = t;
   a.table = (const R*)ctx->table;
   a.class_axis = ctx->class_axis;
   a.n_sub = ctx->opt.n_sub;

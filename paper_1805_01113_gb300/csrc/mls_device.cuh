@@ -232,7 +232,9 @@ __device__ __forceinline__ void sym_mul(const R a[10], const R y[4], R out[4]) {
   out[3] = a[6] * y[0] + a[7] * y[1] + a[8] * y[2] + a[9] * y[3];
 }
 
-// 1-norm condition number of the packed SPD matrix from its Cholesky factor.
+// 1-norm condition number of the packed SPD matrix from its Cholesky factor:
+// ||A||_1 ||A^-1||_1 with A^-1 = M^T M, M = L^-1 (lower triangular, formed
+// column by column from L M = I).
 template <typename R>
 __device__ __forceinline__ R cond1(const R a[10], const Chol4<R>& ch) {
   R colsum[4] = {
@@ -240,15 +242,26 @@ __device__ __forceinline__ R cond1(const R a[10], const Chol4<R>& ch) {
       fabs(a[1]) + fabs(a[2]) + fabs(a[4]) + fabs(a[7]),
       fabs(a[3]) + fabs(a[4]) + fabs(a[5]) + fabs(a[8]),
       fabs(a[6]) + fabs(a[7]) + fabs(a[8]) + fabs(a[9])};
-  R an = fmax(fmax(colsum[0], colsum[1]), fmax(colsum[2], colsum[3]));
-  R inv_n = R(0);
-  for (int c = 0; c < 4; ++c) {
-    R e[4] = {R(0), R(0), R(0), R(0)};
-    e[c] = R(1);
-    R y[4];
-    ch.solve(e, y);
-    inv_n = fmax(inv_n, fabs(y[0]) + fabs(y[1]) + fabs(y[2]) + fabs(y[3]));
-  }
+  const R an = fmax(fmax(colsum[0], colsum[1]), fmax(colsum[2], colsum[3]));
+  const R m00 = ch.i0, m11 = ch.i1, m22 = ch.i2, m33 = ch.i3;
+  const R m10 = -ch.l10 * m00 * m11;
+  const R m21 = -ch.l21 * m11 * m22;
+  const R m20 = -(ch.l20 * m00 + ch.l21 * m10) * m22;
+  const R m32 = -ch.l32 * m22 * m33;
+  const R m31 = -(ch.l31 * m11 + ch.l32 * m21) * m33;
+  const R m30 = -(ch.l30 * m00 + ch.l31 * m10 + ch.l32 * m20) * m33;
+  const R b00 = m00 * m00 + m10 * m10 + m20 * m20 + m30 * m30;
+  const R b01 = m10 * m11 + m20 * m21 + m30 * m31;
+  const R b02 = m20 * m22 + m30 * m32;
+  const R b03 = m30 * m33;
+  const R b11 = m11 * m11 + m21 * m21 + m31 * m31;
+  const R b12 = m21 * m22 + m31 * m32;
+  const R b13 = m31 * m33;
+  const R b22 = m22 * m22 + m32 * m32;
+  const R b23 = m32 * m33;
+  const R b33 = m33 * m33;
+  const R inv_n = fmax(fmax(fabs(b00) + fabs(b01) + fabs(b02) + fabs(b03), fabs(b01) + fabs(b11) + fabs(b12) + fabs(b13)),
+                       fmax(fabs(b02) + fabs(b12) + fabs(b22) + fabs(b23), fabs(b03) + fabs(b13) + fabs(b23) + fabs(b33)));
   return an * inv_n;
 }
 
@@ -333,6 +346,36 @@ __device__ __forceinline__ void exact_emit(const AxisNodes<R> s[3], const R w[3]
 #pragma unroll
       for (int a = 0; a < 3; ++a) sink(a, b, c, (w[0][a] * wyz) * (gx[a] + gyz));
     }
+}
+
+// c_l of Eq. 8 for an exact-MLS marker without forming the 27 terms: with
+// phi_abc = X_a Y_b Z_c (y0 + y1 xi_x,a + y2 xi_y,b + y3 xi_z,c) (the Gaussian
+// W = X Y Z is separable) and node widths Dx_a, Dy_b, Dz_c, the sums
+// sum_k phi_k Dx_k, sum_k phi_k Dy_k, sum_k phi_k Dz_k and sum_k phi_k dV_k
+// factorise into the per-axis sums S0 = sum_a W_a, S1 = sum_a W_a xi_a,
+// Q0 = sum_a W_a D_a and Q1 = sum_a W_a xi_a D_a (the same sums, reassociated).
+// Returns 0 when sum_k phi_k dV_k is 0.
+template <typename R>
+__device__ __forceinline__ R exact_scale(const AxisNodes<R> s[3], const R w[3][3], const R y[4], R area) {
+  R S0[3], S1[3], Q0[3], Q1[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    S0[d] = S1[d] = Q0[d] = Q1[d] = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R W = w[d][a], Wxi = W * s[d].xi[a];
+      S0[d] += W;
+      S1[d] += Wxi;
+      Q0[d] += W * s[d].w[a];
+      Q1[d] += Wxi * s[d].w[a];
+    }
+  }
+  const R hx = S0[1] * S0[2] * (y[0] * Q0[0] + y[1] * Q1[0]) + (y[2] * S1[1] * S0[2] + y[3] * S0[1] * S1[2]) * Q0[0];
+  const R hy = S0[0] * S0[2] * (y[0] * Q0[1] + y[2] * Q1[1]) + (y[1] * S1[0] * S0[2] + y[3] * S0[0] * S1[2]) * Q0[1];
+  const R hz = S0[0] * S0[1] * (y[0] * Q0[2] + y[3] * Q1[2]) + (y[1] * S1[0] * S0[1] + y[2] * S0[0] * S1[1]) * Q0[2];
+  const R vol = Q0[0] * Q0[1] * Q0[2] * y[0] + Q1[0] * Q0[1] * Q0[2] * y[1] + Q0[0] * Q1[1] * Q0[2] * y[2] +
+                Q0[0] * Q0[1] * Q1[2] * y[3];
+  return vol != R(0) ? (area * ((hx + hy + hz) / R(3))) / vol : R(0);
 }
 
 // All 27 exact shape functions (table path).
