@@ -148,43 +148,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __r
   if (threadIdx.x == 0) tile_sums[ntiles + blockIdx.x] = total;
 }
 
-// Exclusive scan of both per-tile sums (one block); the total of the second
-// is the length of the non-empty tile list.
-__global__ void __launch_bounds__(1024) k_scan_tiles(int32_t* __restrict__ tile_sums, int ntiles,
-                                                     int32_t* __restrict__ n_items) {
-  __shared__ int warp_tot[32];
-  __shared__ int total;
-  constexpr int per = kScanMaxTiles / 1024;
-  for (int part = 0; part < 2; ++part) {
-    int32_t* ts = tile_sums + part * ntiles;
-    int v[per];
-    int s = 0;
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const int i = threadIdx.x * per + q;
-      v[q] = i < ntiles ? ts[i] : 0;
-      s += v[q];
-    }
-    int run = block_exclusive_scan(s, warp_tot, &total);
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const int i = threadIdx.x * per + q;
-      if (i < ntiles) ts[i] = run;
-      run += v[q];
-    }
-    if (part == 1 && threadIdx.x == 0) *n_items = total;
-    __syncthreads();
-  }
-}
-
 // Bin offsets (exclusive prefix of the counts) and the ascending list of
-// non-empty spreading tiles.
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* __restrict__ counts, int nbins,
-                                                             int ntiles, const int32_t* __restrict__ tile_sums,
+// non-empty spreading tiles.  Each block first sums the per-scan-tile totals
+// of the blocks before it (at most kScanMaxTiles values); the last block also
+// writes the length of the tile list.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* __restrict__ counts, int nbins, int ntiles,
+                                                             const int32_t* __restrict__ tile_sums,
                                                              int32_t* __restrict__ offsets,
-                                                             int32_t* __restrict__ items) {
+                                                             int32_t* __restrict__ items,
+                                                             int32_t* __restrict__ n_items) {
   __shared__ int warp_tot[32];
   __shared__ int total;
+  int pc = 0, pi = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanThreads) {
+    pc += tile_sums[t];
+    pi += tile_sums[ntiles + t];
+  }
+  block_exclusive_scan(pc, warp_tot, &total);
+  const int prefix_c = total;
+  __syncthreads();
+  block_exclusive_scan(pi, warp_tot, &total);
+  const int prefix_i = total;
+  __syncthreads();
   const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
   int v[kScanPer];
   int s = 0, ne = 0;
@@ -194,9 +179,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t* __re
     s += v[q];
     ne += (v[q] > 0 && base + q < nbins - 1) ? 1 : 0;
   }
-  int run = block_exclusive_scan(s, warp_tot, &total) + tile_sums[blockIdx.x];
+  int run = block_exclusive_scan(s, warp_tot, &total) + prefix_c;
   __syncthreads();
-  int pos = block_exclusive_scan(ne, warp_tot, &total) + tile_sums[ntiles + blockIdx.x];
+  int pos = block_exclusive_scan(ne, warp_tot, &total) + prefix_i;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_items = prefix_i + total;
 #pragma unroll
   for (int q = 0; q < kScanPer; ++q) {
     if (base + q < nbins) {
@@ -212,11 +198,9 @@ cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx
   int slot = timer_begin(ctx, "scan_reduce", s);
   k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, ntiles, T->tile_sums);
   timer_end(ctx, slot, s);
-  slot = timer_begin(ctx, "scan_tiles", s);
-  k_scan_tiles<<<1, 1024, 0, s>>>(T->tile_sums, ntiles, T->n_items);
-  timer_end(ctx, slot, s);
   slot = timer_begin(ctx, "scan_apply", s);
-  k_scan_apply<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, ntiles, T->tile_sums, T->offsets, T->items);
+  k_scan_apply<<<ntiles, kScanThreads, 0, s>>>(T->counts, nbins, ntiles, T->tile_sums, T->offsets, T->items,
+                                               T->n_items);
   timer_end(ctx, slot, s);
   return cudaGetLastError();
 }
