@@ -168,6 +168,15 @@ __device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 
 // stencil in its own order: x rotated by lane % 3 and z by (lane / 3) % 3;
 // at step (cz, cy, cx) the lane adds node ((cz + rc) % 3, cy, (cx + ra) % 3).
 // The integer sums do not depend on the order.
+// Picks a (r == 0), b (r == 1) or c (r == 2) with two predicated selects,
+// so that the rotation below stays branch-free (lanes differ in r).
+__device__ __forceinline__ float select3(int r, float a, float b, float c) {
+  float bc, o;
+  asm("{\n\t.reg .pred q;\n\tsetp.eq.s32 q, %1, 1;\n\tselp.f32 %0, %2, %3, q;\n\t}" : "=f"(bc) : "r"(r), "f"(b), "f"(c));
+  asm("{\n\t.reg .pred q;\n\tsetp.eq.s32 q, %1, 0;\n\tselp.f32 %0, %2, %3, q;\n\t}" : "=f"(o) : "r"(r), "f"(a), "f"(bc));
+  return o;
+}
+
 __device__ __forceinline__ void add_stencil_fixed(int* a0, const float p[27], float q0, float q1, float q2, int PS,
                                                   int AX, int ACC) {
   const int lane = threadIdx.x & 31;
@@ -176,9 +185,9 @@ __device__ __forceinline__ void add_stencil_fixed(int* a0, const float p[27], fl
 #pragma unroll
   for (int r = 0; r < 9; ++r) {
     const float v0 = p[3 * r], v1 = p[3 * r + 1], v2 = p[3 * r + 2];
-    t[3 * r] = ra == 0 ? v0 : (ra == 1 ? v1 : v2);
-    t[3 * r + 1] = ra == 0 ? v1 : (ra == 1 ? v2 : v0);
-    t[3 * r + 2] = ra == 0 ? v2 : (ra == 1 ? v0 : v1);
+    t[3 * r] = select3(ra, v0, v1, v2);
+    t[3 * r + 1] = select3(ra, v1, v2, v0);
+    t[3 * r + 2] = select3(ra, v2, v0, v1);
   }
   const int xo[3] = {ra, ra == 2 ? 0 : ra + 1, ra == 0 ? 2 : ra - 1};
   const int zo[3] = {rc * PS, (rc == 2 ? 0 : rc + 1) * PS, (rc == 0 ? 2 : rc - 1) * PS};
@@ -191,7 +200,7 @@ __device__ __forceinline__ void add_stencil_fixed(int* a0, const float p[27], fl
 #pragma unroll
       for (int cx = 0; cx < 3; ++cx) {
         const int m = 3 * cy + cx;
-        const float pk = rc == 0 ? t[9 * cz + m] : (rc == 1 ? t[9 * z1 + m] : t[9 * z2 + m]);
+        const float pk = select3(rc, t[9 * cz + m], t[9 * z1 + m], t[9 * z2 + m]);
         int* a = ar + xo[cx];
         atomicAdd(a, round_small(pk * q0));
         atomicAdd(a + ACC, round_small(pk * q1));
