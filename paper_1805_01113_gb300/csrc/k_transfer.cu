@@ -167,7 +167,7 @@ static const void* interp_kernel(int lx) {
 // of the field ([ox-4, ox+2^l+4)) and flushed with 16-byte vector atomics
 // (zero lanes of a group add nothing).  A chunk with non-finite forces is
 // added directly.
-template <typename FT, bool VEC, int LX>
+template <typename FT, bool VEC, int LX, int LY = 0, int LZ = 0>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, const float* __restrict__ phi,
                                                            const float* __restrict__ cl,
                                                            const int32_t* __restrict__ home,
@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int XOFF = VEC ? 4 : 1;
   constexpr int AX = (1 << LX) + 2 * XOFF;
-  const AccShape A(LX, tl.l[1], tl.l[2], VEC);
-  const SpreadSmem L(4, LX, tl.l[1], tl.l[2], VEC);
+  const int ly = LY ? LY : tl.l[1], lz = LZ ? LZ : tl.l[2];   // compile-time when specialised
+  const AccShape A(LX, ly, lz, VEC);
+  const SpreadSmem L(4, LX, ly, lz, VEC);
   const int AY = A.AY, PS = A.PS, ACC = A.ACC, ROWS = AY * A.AZ;
   int* acc = reinterpret_cast<int*>(smem_raw);
   int* row_a = reinterpret_cast<int*>(smem_raw + L.rows);
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
     const int b = items[it];
     const int start = offsets[b], cnt = counts[b];
     const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
-    const int ox = bx << LX, oy = by << tl.l[1], oz = bz << tl.l[2];
+    const int ox = bx << LX, oy = by << ly, oz = bz << lz;
     for (int r = tid; r < ROWS; r += kSpreadThreads) {
       const int ey = r % AY, ez = r / AY;
       row_a[r] = ez * PS + ey * AX;
@@ -422,7 +423,16 @@ static cudaError_t configure_kernel(mls_ctx* ctx, K kernel, int smem) {
 }
 
 template <typename FT, bool VEC>
-static const void* spread_kernel(int lx) {
+static const void* spread_kernel(int lx, int ly, int lz) {
+  // Tile shapes the tile-shape tuner tries get compile-time accumulator strides.
+  if (VEC) {
+    if (lx == 3 && ly == 3 && lz == 3) return (const void*)k_spread<FT, VEC, 3, 3, 3>;
+    if (lx == 3 && ly == 3 && lz == 2) return (const void*)k_spread<FT, VEC, 3, 3, 2>;
+    if (lx == 4 && ly == 3 && lz == 3) return (const void*)k_spread<FT, VEC, 4, 3, 3>;
+    if (lx == 4 && ly == 4 && lz == 3) return (const void*)k_spread<FT, VEC, 4, 4, 3>;
+    if (lx == 4 && ly == 4 && lz == 2) return (const void*)k_spread<FT, VEC, 4, 4, 2>;
+    if (lx == 5 && ly == 3 && lz == 3) return (const void*)k_spread<FT, VEC, 5, 3, 3>;
+  }
   switch (lx) {
     case 1: return VEC ? nullptr : (const void*)k_spread<FT, false, 1>;
     case 2: return (const void*)k_spread<FT, VEC, 2>;
@@ -453,17 +463,17 @@ cudaError_t spread_configure(mls_ctx* ctx) {
   const cudaError_t ei = interp_configure(ctx);
   if (ei != cudaSuccess) return ei;
   const int smem = (int)spread_smem_bytes(ctx);
-  const int lx = ctx->tiles.l[0];
+  const int lx = ctx->tiles.l[0], ly = ctx->tiles.l[1], lz = ctx->tiles.l[2];
   if (ctx->opt.real == MLS_F64) return configure_kernel(ctx, k_spread_f64, smem);
   const bool bf = ctx->opt.field == MLS_BF16;
   if (spread_vec(ctx)) {
     // The scalar variant also runs when f is not aligned for the vector reductions (same layout size or smaller).
-    cudaError_t e = configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, false>(lx) : spread_kernel<float, false>(lx),
+    cudaError_t e = configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, false>(lx, ly, lz) : spread_kernel<float, false>(lx, ly, lz),
                                      smem);
     if (e != cudaSuccess) return e;
-    return configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, true>(lx) : spread_kernel<float, true>(lx), smem);
+    return configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, true>(lx, ly, lz) : spread_kernel<float, true>(lx, ly, lz), smem);
   }
-  return configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, false>(lx) : spread_kernel<float, false>(lx), smem);
+  return configure_kernel(ctx, bf ? spread_kernel<__nv_bfloat16, false>(lx, ly, lz) : spread_kernel<float, false>(lx, ly, lz), smem);
 }
 
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s) {
@@ -496,7 +506,7 @@ static cudaError_t launch_spread_one(const mls_ctx* ctx, const mls_transfer* T, 
   int64_t M = T->M, cap = T->cap;
   void* args[] = {&D, &tl, (void*)&phi, (void*)&c, (void*)&T->home, (void*)&T->perm, (void*)&T->items,
                   (void*)&T->n_items, (void*)&T->offsets, (void*)&T->counts, &M, &cap, (void*)&F, &f};
-  return cudaLaunchKernel(spread_kernel<FT, VEC>(tl.l[0]), dim3(ctx->spread_grid), dim3(ctx->spread_threads), args,
+  return cudaLaunchKernel(spread_kernel<FT, VEC>(tl.l[0], tl.l[1], tl.l[2]), dim3(ctx->spread_grid), dim3(ctx->spread_threads), args,
                           spread_smem_bytes(ctx), s);
 }
 
