@@ -33,7 +33,7 @@ struct ForceSmem {
 // added directly); the flagged rows are flushed with vector reductions (VEC)
 // or scalar atomics and reset.  Markers without support (the last bin of the
 // tile sort) get U = F = 0.
-template <typename FT, bool VEC, int LX>
+template <typename FT, bool VEC, int LX, int LY = 0, int LZ = 0>
 __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
     Dims D, Tiles tl, const float* __restrict__ phi, const float* __restrict__ cl, const int32_t* __restrict__ home,
     const int32_t* __restrict__ perm, const int32_t* __restrict__ items, const int32_t* __restrict__ n_items_p,
@@ -44,9 +44,10 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
   constexpr int XOFF = VEC ? 4 : 1;
   constexpr int AX = (1 << LX) + 2 * XOFF;
   constexpr int BX = (1 << LX) + 2;
-  const AccShape A(LX, tl.l[1], tl.l[2], VEC);
-  const InterpSmem B(LX, tl.l[1], tl.l[2]);
-  const ForceSmem L(LX, tl.l[1], tl.l[2], VEC);
+  const int ly = LY ? LY : tl.l[1], lz = LZ ? LZ : tl.l[2];   // compile-time when specialised
+  const AccShape A(LX, ly, lz, VEC);
+  const InterpSmem B(LX, ly, lz);
+  const ForceSmem L(LX, ly, lz, VEC);
   const int AY = A.AY, PS = A.PS, ACC = A.ACC, ROWS = AY * A.AZ;
   const int BPS = B.PS, CELLS = B.CELLS;
   int* acc = reinterpret_cast<int*>(smem_raw);
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
     const int b = items[it];
     const int start = offsets[b], end = start + counts[b];
     const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
-    const int ox = bx << LX, oy = by << tl.l[1], oz = bz << tl.l[2];
+    const int ox = bx << LX, oy = by << ly, oz = bz << lz;
     // Touched rows of the whole tile (plain byte stores) and the row tables.
     for (int j = start + tid; j < end; j += kSpreadThreads) {
       int i[3];
@@ -278,7 +279,16 @@ __global__ void __launch_bounds__(kBlock) k_force_from_u(const int32_t* __restri
 }
 
 template <typename FT, bool VEC>
-static const void* force_kernel(int lx) {
+static const void* force_kernel(int lx, int ly, int lz) {
+  // Tile shapes the tile-shape tuner tries get compile-time strides.
+  if (VEC) {
+    if (lx == 3 && ly == 3 && lz == 3) return (const void*)k_direct_forcing<FT, VEC, 3, 3, 3>;
+    if (lx == 3 && ly == 3 && lz == 2) return (const void*)k_direct_forcing<FT, VEC, 3, 3, 2>;
+    if (lx == 4 && ly == 3 && lz == 3) return (const void*)k_direct_forcing<FT, VEC, 4, 3, 3>;
+    if (lx == 4 && ly == 4 && lz == 3) return (const void*)k_direct_forcing<FT, VEC, 4, 4, 3>;
+    if (lx == 4 && ly == 4 && lz == 2) return (const void*)k_direct_forcing<FT, VEC, 4, 4, 2>;
+    if (lx == 5 && ly == 3 && lz == 3) return (const void*)k_direct_forcing<FT, VEC, 5, 3, 3>;
+  }
   switch (lx) {
     case 1: return VEC ? nullptr : (const void*)k_direct_forcing<FT, false, 1>;
     case 2: return (const void*)k_direct_forcing<FT, VEC, 2>;
@@ -316,14 +326,14 @@ cudaError_t force_configure(mls_ctx* ctx) {
   if (e != cudaSuccess) return e;
   const int smem = (int)force_smem_bytes(ctx);
   if (smem > optin) return cudaSuccess;
-  const int lx = ctx->tiles.l[0];
+  const int lx = ctx->tiles.l[0], ly = ctx->tiles.l[1], lz = ctx->tiles.l[2];
   const bool bf = ctx->opt.field == MLS_BF16;
   if (spread_vec(ctx)) {
-    e = force_configure_one(ctx, bf ? force_kernel<__nv_bfloat16, false>(lx) : force_kernel<float, false>(lx), smem);
+    e = force_configure_one(ctx, bf ? force_kernel<__nv_bfloat16, false>(lx, ly, lz) : force_kernel<float, false>(lx, ly, lz), smem);
     if (e != cudaSuccess) return e;
-    return force_configure_one(ctx, bf ? force_kernel<__nv_bfloat16, true>(lx) : force_kernel<float, true>(lx), smem);
+    return force_configure_one(ctx, bf ? force_kernel<__nv_bfloat16, true>(lx, ly, lz) : force_kernel<float, true>(lx, ly, lz), smem);
   }
-  return force_configure_one(ctx, bf ? force_kernel<__nv_bfloat16, false>(lx) : force_kernel<float, false>(lx), smem);
+  return force_configure_one(ctx, bf ? force_kernel<__nv_bfloat16, false>(lx, ly, lz) : force_kernel<float, false>(lx, ly, lz), smem);
 }
 
 cudaError_t launch_direct_forcing(const mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb,
@@ -356,8 +366,8 @@ cudaError_t launch_direct_forcing(const mls_ctx* ctx, const mls_transfer* T, con
   float inv_dt = (float)(1.0 / dt);
   const bool vec = spread_vec_aligned(ctx, f);
   const bool bf = ctx->opt.field == MLS_BF16;
-  const void* k = bf ? (vec ? force_kernel<__nv_bfloat16, true>(tl.l[0]) : force_kernel<__nv_bfloat16, false>(tl.l[0]))
-                     : (vec ? force_kernel<float, true>(tl.l[0]) : force_kernel<float, false>(tl.l[0]));
+  const void* k = bf ? (vec ? force_kernel<__nv_bfloat16, true>(tl.l[0], tl.l[1], tl.l[2]) : force_kernel<__nv_bfloat16, false>(tl.l[0], tl.l[1], tl.l[2]))
+                     : (vec ? force_kernel<float, true>(tl.l[0], tl.l[1], tl.l[2]) : force_kernel<float, false>(tl.l[0], tl.l[1], tl.l[2]));
   void* args[] = {&D, &tl, (void*)&phi, (void*)&c, (void*)&T->home, (void*)&T->perm, (void*)&T->items,
                   (void*)&T->n_items, (void*)&T->offsets, (void*)&T->counts, &M, &cap, (void*)&u, (void*)&Vb,
                   &inv_dt, &U, &F, &f};
