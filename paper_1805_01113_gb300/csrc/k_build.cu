@@ -139,10 +139,8 @@ __global__ void __launch_bounds__(kBlock) k_build_exact_redo(BuildArgs<float> a)
 // blend of the 8 corner rows of the table, alpha_i proportional to 1/d_i^2
 // (Eq. 10), evaluated as alpha_i = prod_{j!=i} d_j^2 / sum_i prod_{j!=i} d_j^2
 // which equals it and stays finite when the marker sits on a corner.
-template <typename R>
-__global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.M) return;
+template <typename R, bool SMEM>
+__device__ __forceinline__ void fast_marker(const BuildArgs<R>& a, int64_t j, const R* __restrict__ table) {
   int h[3];
   R p[3], ar;
   AxisNodes<R> s[3];
@@ -179,7 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
   }
   const R inv = R(1) / sum;
   const int cl = a.class_axis >= 0 ? h[a.class_axis] : 0;
-  const R* T = a.table + ((int64_t)cl * n * n * n + (int64_t)(((sc[2] * n) + sc[1]) * n + sc[0])) * kTableRow;
+  const R* T = table + ((int64_t)cl * n * n * n + (int64_t)(((sc[2] * n) + sc[1]) * n + sc[0])) * kTableRow;
   // Corner q sits at sub-node offset (q&1, (q>>1)&1, q>>2) from the sub-cell origin.
   int64_t roff[8];
 #pragma unroll
@@ -199,7 +197,8 @@ __global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
     for (int e = 0; e < kVec; ++e) acc[e] = R(0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const V t = __ldg(reinterpret_cast<const V*>(T + roff[q]) + v);
+      const V* tp = reinterpret_cast<const V*>(T + roff[q]) + v;
+      const V t = SMEM ? *tp : __ldg(tp);
       const R* tv = reinterpret_cast<const R*>(&t);
 #pragma unroll
       for (int e = 0; e < kVec; ++e) acc[e] += alpha[q] * tv[e];
@@ -214,6 +213,30 @@ __global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
     }
   }
   marker_finish(a, j, h, s, sums, ar);
+}
+
+// Fast-MLS build (Eqs. 9-10), one thread per marker, table rows read through
+// the read-only cache.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_build_fast(BuildArgs<R> a) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.M) return;
+  fast_marker<R, false>(a, j, a.table);
+}
+
+// The same for a table that fits in shared memory (one class: grids uniform
+// in all three axes): persistent blocks copy it once and read the 8 corner
+// rows of every marker from shared memory instead of scattered cache lines.
+// Blocks are larger than kBlock so that the two that fit per SM beside their
+// table copies keep enough warps resident (two blocks of 512 at 64 registers).
+constexpr int kFastSmemThreads = 512;
+__global__ void __launch_bounds__(kFastSmemThreads, 2) k_build_fast_smem(BuildArgs<float> a, int table_vec4) {
+  extern __shared__ float4 tab_s[];
+  const float4* src = reinterpret_cast<const float4*>(a.table);
+  for (int q = threadIdx.x; q < table_vec4; q += blockDim.x) tab_s[q] = src[q];
+  __syncthreads();
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.M; j += (int64_t)gridDim.x * blockDim.x)
+    fast_marker<float, true>(a, j, reinterpret_cast<const float*>(tab_s));
 }
 
 // Table of exact shape functions at the sub-Eulerian nodes -1/2 + i/(n-1)
@@ -298,9 +321,37 @@ cudaError_t launch_build_fast(const mls_ctx* ctx, mls_transfer* T, const void* x
   const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
   if (ctx->opt.real == MLS_F64)
     k_build_fast<double><<<grid, kBlock, 0, s>>>(make_args<double>(ctx, T, x, area, M));
-  else
+  else if (ctx->fast_smem_grid > 0 && ctx->n_classes == 1) {
+    const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
+    const int vec4 = (int)(S3 * kTableRow / 4);
+    const unsigned g =
+        (unsigned)std::min<int64_t>(ctx->fast_smem_grid, (M + kFastSmemThreads - 1) / kFastSmemThreads);
+    k_build_fast_smem<<<g, kFastSmemThreads, (size_t)vec4 * 16, s>>>(make_args<float>(ctx, T, x, area, M), vec4);
+  } else
     k_build_fast<float><<<grid, kBlock, 0, s>>>(make_args<float>(ctx, T, x, area, M));
   return cudaGetLastError();
+}
+
+// The shared-memory fast build is used when the single-precision table has
+// one class and leaves room for two blocks per SM; its persistent grid is the
+// resident block count.
+cudaError_t build_configure(mls_ctx* ctx) {
+  ctx->fast_smem_grid = 0;
+  if (ctx->opt.real != MLS_F32 || !(ctx->uniform[0] && ctx->uniform[1] && ctx->uniform[2])) return cudaSuccess;
+  const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
+  const int64_t bytes = S3 * kTableRow * 4;
+  if (bytes > 100 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_build_fast_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_fast_smem, kFastSmemThreads,
+                                                     (size_t)bytes)) !=
+      cudaSuccess)
+    return e;
+  ctx->fast_smem_grid = per_sm > 0 ? per_sm * sms : 0;
+  return cudaSuccess;
 }
 
 cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s) {

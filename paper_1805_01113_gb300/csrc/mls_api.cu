@@ -219,6 +219,7 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
   cudaError_t e = spread_configure(c);
   if (e == cudaSuccess) e = force_configure(c);
   if (e == cudaSuccess) e = collision_configure(c);
+  if (e == cudaSuccess) e = build_configure(c);
   if (e == cudaSuccess) e = mlp_configure();
   if (e != cudaSuccess) {
     free_ctx(c);

@@ -45,6 +45,7 @@ struct mls_ctx {
   int interp_grid;       // persistent grid of the tile-organised interpolation
   int force_grid;        // persistent grid of the fused direct-forcing kernel (0: composed path)
   int collision_grid;    // persistent grid of the collision detection
+  int fast_smem_grid;    // persistent grid of the shared-memory fast-MLS build (0: not used)
   void* refine_ws;       // refinement workspace (grown on demand)
   int64_t refine_ws_bytes;
   // Learned surrogate: float32 parameters and the packed bfloat16 copy.
@@ -113,6 +114,7 @@ cudaError_t force_configure(mls_ctx* ctx);
 cudaError_t launch_collisions(const mls_ctx* ctx, const mls_transfer* T, const int32_t* body, int32_t* flag,
                               int32_t* coll, unsigned long long* n_colliding, cudaStream_t s);
 cudaError_t collision_configure(mls_ctx* ctx);
+cudaError_t build_configure(mls_ctx* ctx);
 int64_t refine_workspace_bytes(int64_t nt);
 cudaError_t launch_refine(const mls_ctx* ctx, const void* V, int64_t nv, const int32_t* tri, int64_t nt,
                           double ratio, int max_level, int64_t capacity, void* x, void* area, int32_t* parent,
