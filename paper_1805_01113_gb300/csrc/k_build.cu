@@ -340,8 +340,9 @@ cudaError_t build_configure(mls_ctx* ctx) {
   if (ctx->opt.real != MLS_F32 || !(ctx->uniform[0] && ctx->uniform[1] && ctx->uniform[2])) return cudaSuccess;
   const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
   const int64_t bytes = S3 * kTableRow * 4;
-  if (bytes > 100 * 1024) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_build_fast_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  constexpr int kMaxTableBytes = 100 * 1024;
+  if (bytes > kMaxTableBytes) return cudaSuccess;
+  cudaError_t e = raise_smem_limit((const void*)k_build_fast_smem, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0, dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

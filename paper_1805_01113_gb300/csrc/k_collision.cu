@@ -94,9 +94,7 @@ cudaError_t collision_configure(mls_ctx* ctx) {
   const int* l = ctx->tiles.l;
   const int smem = 4 << (l[0] + l[1] + l[2]);
   cudaError_t e;
-  if (smem > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(k_collisions, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-    return e;
+  if ((e = raise_smem_limit((const void*)k_collisions, smem)) != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collisions, kSpreadThreads, smem)) != cudaSuccess)

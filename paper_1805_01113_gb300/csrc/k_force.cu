@@ -305,9 +305,7 @@ size_t force_smem_bytes(const mls_ctx* ctx) {
 
 static cudaError_t force_configure_one(mls_ctx* ctx, const void* k, int smem) {
   cudaError_t e;
-  if (smem > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-    return e;
+  if ((e = raise_smem_limit(k, smem)) != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSpreadThreads, smem)) != cudaSuccess) return e;

@@ -409,8 +409,7 @@ size_t spread_smem_bytes(const mls_ctx* ctx) {
 
 template <typename K>
 static cudaError_t configure_kernel(mls_ctx* ctx, K kernel, int smem) {
-  cudaError_t e = cudaSuccess;
-  if (smem > 48 * 1024) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = raise_smem_limit((const void*)kernel, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0, dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -448,9 +447,7 @@ static cudaError_t interp_configure(mls_ctx* ctx) {
   const void* k = ctx->opt.field == MLS_F32 ? interp_kernel<float>(ctx->tiles.l[0])
                                             : interp_kernel<__nv_bfloat16>(ctx->tiles.l[0]);
   cudaError_t e;
-  if (smem > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-    return e;
+  if ((e = raise_smem_limit(k, smem)) != cudaSuccess) return e;
   int per_sm = 0, sms = 0, dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

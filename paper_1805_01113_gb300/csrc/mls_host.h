@@ -87,6 +87,19 @@ constexpr int kSpreadThreads = 128;   // threads per block of the spreading kern
 constexpr int kTableRow = 28;         // fast-MLS table row: 27 shape-function values + 1 pad (16-byte rows)
 constexpr int kInterpThreads = 128;   // threads per block of the tile-organised interpolation
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (above the
+// 48 KB default).  The limit belongs to the kernel, shared by every context of
+// the process, so it is only ever raised: a context with smaller tiles must
+// not lower it under one configured earlier.
+inline cudaError_t raise_smem_limit(const void* kernel, int bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
