@@ -27,13 +27,15 @@ __device__ __forceinline__ R moment_entry(const R S[4][3], int i, int j, int ext
 // (xi in home-cell widths Delta_d, Gaussian weight).  A and the three d_d A
 // are assembled from per-axis moments up to the third; the Cholesky factor of
 // A (one refinement step for gamma in single precision) serves all four
-// solves.  Markers without support get G = 0.
+// solves.  Markers without support get G = 0.  In single precision the kernel
+// is held to 128 registers so two blocks fit per SM: the 81 gathers of a
+// marker go straight to the cache hierarchy, and one block per SM (the
+// unbounded 142 registers) leaves too few warps to cover them.
 template <typename R, typename FT>
-__global__ void __launch_bounds__(kBlock) k_interp_gradient(Dims D, Grid<R> g, const R* __restrict__ x,
-                                                            const int32_t* __restrict__ home,
-                                                            const int32_t* __restrict__ perm, int64_t M,
-                                                            R inv_eps2, int refine, const FT* __restrict__ u,
-                                                            R* __restrict__ G) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1)
+    k_interp_gradient(Dims D, Grid<R> g, const R* __restrict__ x, const int32_t* __restrict__ home,
+                      const int32_t* __restrict__ perm, int64_t M, R inv_eps2, int refine,
+                      const FT* __restrict__ u, R* __restrict__ G) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   const int64_t m = perm[j];
