@@ -308,6 +308,24 @@ def test_rebuild_with_other_markers(api):
         assert normwise(got["f"], ref["f"]) <= TOL["f32"]
 
 
+def test_contexts_with_large_tiles_keep_their_shared_memory(api):
+    """A kernel's dynamic shared-memory limit is shared by every context: a
+    context created later with smaller (but still large) tiles of the same
+    kernel must not lower it under an earlier one.  Tiles 4,4,4 need about
+    97 KB of spreading accumulator, tiles 4,3,4 about 54 KB."""
+    w = make_workload("c2", n=64, n_bodies=6)
+    grid = oracle.Grid(w.faces, w.periodic)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    u = field_full_np(w.modes, w.faces, np.float32)
+    F = w.forces().astype(np.float32)
+    big = api.Context(w.faces, w.periodic, real="f32", brick_log2=(4, 4, 4))
+    small = api.Context(w.faces, w.periodic, real="f32", brick_log2=(4, 3, 4))
+    r = run_oracle(grid, x, area, "exact", u, F)
+    for ctx in (big, small, big):
+        g = run_gpu(ctx, x, area, "exact", torch.as_tensor(u, device=DEV), F)
+        _compare(g, r, TOL["f32"])
+
+
 def _neighbour_markers(home3, n, cell):
     """Indices of markers whose home cell lies within +/-1 (periodic) of `cell`."""
     d = [(home3[a] - cell[a] + 1) % n[a] for a in range(3)]
