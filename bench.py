@@ -4,7 +4,9 @@ Default workload: 2000 ellipsoids of 1280 markers each (2.56 M markers) in a
 uniform periodic 512^3 grid, single precision, exact-MLS (the fast-MLS step
 is timed alongside and reported under "fast").  Inputs are synthetic and
 resident in HBM before timing; L2 is flushed (256 MiB write) between timed
-steps, outside the timed events.  One JSON line on stdout (rank 0).
+steps, outside the timed events.  Each step is replayed from a CUDA graph
+captured once (--no-graph: plain stream-ordered calls; both are reported).
+One JSON line on stdout (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload c2|c3|c1] [--method exact|fast]
@@ -64,7 +66,8 @@ def parse():
     p.add_argument("--sample-bodies", type=int, default=160, help="bodies in the CPU oracle sample")
     p.add_argument("--grid", type=int, default=None, help="cells per axis (smaller profiling cases)")
     p.add_argument("--bodies", type=int, default=None, help="number of bodies (smaller profiling cases)")
-    p.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    p.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph (the default)")
+    p.add_argument("--no-graph", action="store_true", help="issue every step as plain stream-ordered calls")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tiles", default=None, help="spreading tile log2 sizes, e.g. 3,3,2 (skips the autotuner)")
     p.add_argument("--no-surrogate", action="store_true")
@@ -333,11 +336,16 @@ def run_ours(a, rank, world, local):
     touched = int(torch.count_nonzero(f[0]).item())
     u_cells = touched / M
 
+    # A step is replayed from a CUDA graph captured once per method (the
+    # library's calls are stream-ordered and allocate nothing in a step), as a
+    # solver that captures its time step would run it; --no-graph issues the
+    # calls one by one.  A failed capture falls back to plain calls.
     graphs = {}
+    graph_state = {"use": not a.no_graph, "error": None}
 
     def run_step(method):
-        if a.graph:
-            if method not in graphs:
+        if graph_state["use"] and method not in graphs:
+            try:
                 for _ in range(2):
                     step(method)
                 torch.cuda.synchronize()
@@ -345,17 +353,22 @@ def run_ours(a, rank, world, local):
                 with torch.cuda.graph(g):
                     step(method)
                 graphs[method] = g
+            except Exception as ex:  # reported in config; the plain calls below still run the step
+                graph_state["use"], graph_state["error"] = False, str(ex)[:200]
+                torch.cuda.synchronize()
+        if graph_state["use"]:
             graphs[method].replay()
         else:
             step(method)
 
-    def timed(method, steps, warmup, per_kernel, min_warm_s=0.0):
+    def timed(method, steps, warmup, per_kernel, min_warm_s=0.0, plain=False):
         # At least `warmup` untimed steps, and at least min_warm_s of load so the
         # clock sampler sees the GPU busy around the timed region.
         t0 = time.perf_counter()
         done = 0
+        direct = per_kernel or plain
         while done < warmup or time.perf_counter() - t0 < min_warm_s:
-            run_step(method) if not per_kernel else step(method)
+            step(method) if direct else run_step(method)
             done += 1
             if done % 16 == 0:
                 torch.cuda.synchronize()
@@ -370,7 +383,7 @@ def run_ours(a, rank, world, local):
         for e0, e1 in evs:
             flush.fill_(1.0)
             e0.record(stream)
-            step(method) if per_kernel else run_step(method)
+            step(method) if direct else run_step(method)
             e1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -387,6 +400,12 @@ def run_ours(a, rank, world, local):
     clocks = clk.stop()
     total_ms = max_over_ranks(sum(ms), world, dev)
     value = job_throughput(M, world, a.steps, total_ms)
+    # the same step issued as plain stream-ordered calls (reported beside the headline)
+    stream_calls = None
+    if graph_state["use"]:
+        ms_p, _ = timed(a.method, a.steps, 3, False, plain=True)
+        tp = max_over_ranks(sum(ms_p), world, dev)
+        stream_calls = {"value": job_throughput(M, world, a.steps, tp), "ms_per_step": tp / a.steps}
 
     # per-kernel pass (events around each kernel on the launching stream)
     ms_k, kt = timed(a.method, a.steps, 2, True)
@@ -683,11 +702,11 @@ def run_ours(a, rank, world, local):
                    "markers_per_gpu": M, "method": a.method, "grid": list(w.n),
                    "l2": "flushed by a 256 MiB write before every timed step",
                    "step": "marker_prep + build_transfer + interpolate + spread",
-                   "graph": bool(a.graph), "tiles_log2": list(tiles),
+                   "graph": graph_state["use"], "graph_error": graph_state["error"], "tiles_log2": list(tiles),
                    "autotune_ms": {str(k): round(v, 4) for k, v in tune_ms.items()} if tune_ms else None,
                    "touched_cells_per_marker": round(u_cells, 4)},
         "roofline": roof, "kernels": kernels, "gpu_launches": launches, "methods": others,
-        "precision": precision, "e2e": e2e, "clocks": clocks, "cpu_baseline": cpu,
+        "precision": precision, "e2e": e2e, "stream_calls": stream_calls, "clocks": clocks, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line))
