@@ -603,9 +603,19 @@ def run_ours(a, rank, world, local):
                 torch.cuda.synchronize()
                 tg.append(time.perf_counter() - t0)
             e2e["graph"] = {"value": M * world / statistics.median(tg), "ms_per_step": 1e3 * statistics.mean(tg),
-                            "ms_per_step_median": 1e3 * statistics.median(tg)}
+                            "ms_per_step_median": 1e3 * statistics.median(tg), "ms_per_step_min": 1e3 * min(tg)}
         except Exception as ex:  # reported, not fatal: the plain figure above stands
             e2e["graph"] = {"error": str(ex)[:200]}
+        # Like the device-resident headline, the end-to-end value is the graph
+        # replay when steps are replayed from graphs; the plain calls stay beside it.
+        if graph_state["use"] and "value" in e2e["graph"]:
+            g_ = e2e.pop("graph")
+            keys = ("value", "ms_per_step", "ms_per_step_median", "ms_per_step_min")
+            e2e["stream_calls"] = {k: e2e[k] for k in keys}
+            e2e.update({k: g_[k] for k in keys})
+            e2e["mode"] = "step (copies included) replayed from a CUDA graph captured once"
+        else:
+            e2e["mode"] = "stream-ordered calls"
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only): its timing, and the
     # error of every method and precision mode against it on that sample.
