@@ -2,6 +2,7 @@
 // forward/backward and Adam kernels, and the bfloat16 tensor-core network
 // used by MLS_SURROGATE builds (projection onto linear reproduction, exact
 // fallback).
+#include <algorithm>
 #include <cmath>
 
 #include "mls_host.h"
@@ -401,13 +402,10 @@ struct SurrogateArgs {
   const unsigned char* pack;
 };
 
-__global__ void __launch_bounds__(kMlpThreads) k_build_surrogate(SurrogateArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  load_pack(smem, a.pack);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* feat = reinterpret_cast<float*>(smem + kPackBytes) + warp * (kWarpFeat + kWarpY);
-  float* Y = feat + kWarpFeat;
-  const int64_t j = (int64_t)blockIdx.x * kMlpThreads + threadIdx.x;
+// One marker per lane; the warp's 32 markers share the network evaluation
+// (feat and Y are the warp's own staging buffers, smem holds the weights).
+__device__ __forceinline__ void surrogate_marker(const SurrogateArgs& a, int64_t j, float* feat, float* Y,
+                                                 const unsigned char* smem, int lane) {
   bool ok = j < a.M;
   int h[3] = {0, 0, 0};
   float ar = 0.f;
@@ -449,7 +447,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_build_surrogate(SurrogateArgs a
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) feat[lane * 8 + i] = f[i];
-  __syncthreads();
+  __syncwarp();
   mlp_warp_bf16(feat, Y, smem);
   __syncwarp();
   if (!ok) return;
@@ -523,6 +521,24 @@ __global__ void __launch_bounds__(kMlpThreads) k_build_surrogate(SurrogateArgs a
   a.home[j] = (h[2] * a.g.ax[1].n + h[1]) * a.g.ax[0].n + h[0];
 }
 
+// Persistent blocks: each copies the packed weights into shared memory once
+// and then walks chunks of kMlpThreads markers (one launch of one block per
+// chunk would copy the 16 KB of weights again for every 128 markers).
+__global__ void __launch_bounds__(kMlpThreads) k_build_surrogate(SurrogateArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_pack(smem, a.pack);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* feat = reinterpret_cast<float*>(smem + kPackBytes) + warp * (kWarpFeat + kWarpY);
+  float* Y = feat + kWarpFeat;
+  for (int64_t base = (int64_t)blockIdx.x * kMlpThreads; base < a.M; base += (int64_t)gridDim.x * kMlpThreads) {
+    __syncwarp();  // the previous chunk's reads of feat and Y are done
+    surrogate_marker(a, base + threadIdx.x, feat, Y, smem, lane);
+  }
+}
+
+static int g_surrogate_grid = 0;  // resident blocks of k_build_surrogate on the device (set by mlp_configure)
+
 // ---- host launchers ----------------------------------------------------------------
 static SurrogateAxes surrogate_axes(const mls_ctx* ctx) {
   SurrogateAxes ax;
@@ -572,7 +588,17 @@ cudaError_t mlp_configure() {
   if ((e = cudaFuncSetAttribute(k_mlp_forward_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kBf16Smem)) !=
       cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_build_surrogate, cudaFuncAttributeMaxDynamicSharedMemorySize, kBf16Smem);
+  if ((e = cudaFuncSetAttribute(k_build_surrogate, cudaFuncAttributeMaxDynamicSharedMemorySize, kBf16Smem)) !=
+      cudaSuccess)
+    return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_surrogate, kMlpThreads, kBf16Smem)) !=
+      cudaSuccess)
+    return e;
+  g_surrogate_grid = (per_sm > 0 ? per_sm : 1) * sms;
+  return cudaSuccess;
 }
 
 size_t mlp_pack_bytes() { return kPackBytes; }
@@ -656,7 +682,9 @@ cudaError_t launch_build_surrogate(const mls_ctx* ctx, mls_transfer* T, const vo
   a.inv_eps2 = (float)(1.0 / (ctx->opt.eps * ctx->opt.eps));
   a.residual_max = (float)ctx->opt.residual_max;
   a.pack = ctx->mlp_pack;
-  const unsigned nb = (unsigned)((M + kMlpThreads - 1) / kMlpThreads);
+  const int64_t chunks = (M + kMlpThreads - 1) / kMlpThreads;
+  const int64_t resident = g_surrogate_grid > 0 ? g_surrogate_grid : chunks;
+  const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, resident));
   k_build_surrogate<<<nb, kMlpThreads, kBf16Smem, s>>>(a);
   return cudaGetLastError();
 }
