@@ -1,5 +1,6 @@
 // Euler-to-Lagrange interpolation (gather) and Lagrange-to-Euler spreading
-// (scatter through shared-memory tile accumulators).
+// (scatter through shared-memory tile accumulators in single precision,
+// direct global reductions in double precision).
 #include "transfer_common.cuh"
 
 namespace mls {
@@ -340,70 +341,45 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
   }
 }
 
-// Double-precision spreading: the same tile walk with double shared-memory
-// atomics (used for the small double-precision workloads).
-__global__ void __launch_bounds__(kSpreadThreads) k_spread_f64(Dims D, Tiles tl, const double* __restrict__ phi,
-                                                               const double* __restrict__ cl,
-                                                               const int32_t* __restrict__ home,
-                                                               const int32_t* __restrict__ perm,
-                                                               const int32_t* __restrict__ items,
-                                                               const int32_t* __restrict__ n_items_p,
-                                                               const int32_t* __restrict__ offsets,
-                                                               const int32_t* __restrict__ counts, int64_t M,
-                                                               int64_t cap, const double* __restrict__ F,
-                                                               double* __restrict__ f) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* acc = reinterpret_cast<double*>(smem_raw);
-  const int AX = (1 << tl.l[0]) + 2, AY = (1 << tl.l[1]) + 2, AZ = (1 << tl.l[2]) + 2;
-  const int ACC = AX * AY * AZ;
-  const int tid = threadIdx.x;
+// Double-precision spreading (the small double-precision workloads): one
+// thread per stored marker adds its 27 x 3 terms c_l phi_k F_l straight into
+// f with native global double reductions.  Shared-memory accumulation, as in
+// single precision, needs double shared atomics, which are compare-and-swap
+// loops on this GPU and serialise badly where markers crowd few cells.
+__global__ void __launch_bounds__(kBlock) k_spread_f64(Dims D, const double* __restrict__ phi,
+                                                       const double* __restrict__ cl, const int32_t* __restrict__ home,
+                                                       const int32_t* __restrict__ perm, int64_t M, int64_t cap,
+                                                       const double* __restrict__ F, double* __restrict__ f) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int32_t h = home[j];
+  if (h < 0) return;
+  int i[3];
+  decode_home(h, D, i);
+  const int64_t m = perm[j];
+  const double c = cl[j];
+  const double v0 = c * F[m], v1 = c * F[M + m], v2 = c * F[2 * M + m];
   const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
-  const int n_items = *n_items_p;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int b = items[it];
-    const int start = offsets[b], cnt = counts[b];
-    const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
-    const int ox = bx << tl.l[0], oy = by << tl.l[1], oz = bz << tl.l[2];
-    for (int e = tid; e < 3 * ACC; e += kSpreadThreads) acc[e] = 0.0;
-    __syncthreads();
-    for (int j = start + tid; j < start + cnt; j += kSpreadThreads) {
-      int i[3];
-      decode_home(home[j], D, i);
-      const int64_t m = perm[j];
-      const double c = cl[j];
-      const double v0 = c * F[m], v1 = c * F[M + m], v2 = c * F[2 * M + m];
-      const int lx = i[0] - ox, ly = i[1] - oy, lz = i[2] - oz;
-      for (int cz = 0; cz < 3; ++cz)
-        for (int cy = 0; cy < 3; ++cy)
-          for (int cx = 0; cx < 3; ++cx) {
-            const double p = phi[(9 * cz + 3 * cy + cx) * cap + j];
-            const int li = ((lz + cz) * AY + (ly + cy)) * AX + (lx + cx);
-            atomicAdd(&acc[li], p * v0);
-            atomicAdd(&acc[ACC + li], p * v1);
-            atomicAdd(&acc[2 * ACC + li], p * v2);
-          }
-    }
-    __syncthreads();
-    for (int e = tid; e < ACC; e += kSpreadThreads) {
-      const double a0 = acc[e], a1 = acc[ACC + e], a2 = acc[2 * ACC + e];
-      if (a0 != 0.0 || a1 != 0.0 || a2 != 0.0) {
-        const int ex = e % AX, ey = (e / AX) % AY, ez = e / (AX * AY);
-        const int gx = wrap(ox - 1 + ex, D.n[0], D.periodic[0]);
-        const int gy = wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
-        const int gz = wrap(oz - 1 + ez, D.n[2], D.periodic[2]);
-        const int64_t o = ((int64_t)gz * D.n[1] + gy) * D.n[0] + gx;
-        if (a0 != 0.0) atomicAdd(f + o, a0);
-        if (a1 != 0.0) atomicAdd(f + N + o, a1);
-        if (a2 != 0.0) atomicAdd(f + 2 * N + o, a2);
+#pragma unroll
+  for (int cz = 0; cz < 3; ++cz) {
+    const int gz = wrap(i[2] + cz - 1, D.n[2], D.periodic[2]);
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+      const int64_t row = ((int64_t)gz * D.n[1] + wrap(i[1] + cy - 1, D.n[1], D.periodic[1])) * D.n[0];
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) {
+        const double p = phi[(9 * cz + 3 * cy + cx) * cap + j];
+        const int64_t o = row + wrap(i[0] + cx - 1, D.n[0], D.periodic[0]);
+        atomicAdd(f + o, p * v0);
+        atomicAdd(f + N + o, p * v1);
+        atomicAdd(f + 2 * N + o, p * v2);
       }
     }
-    __syncthreads();
   }
 }
 
 size_t spread_smem_bytes(const mls_ctx* ctx) {
-  if (ctx->opt.real == MLS_F64)
-    return (size_t)SpreadSmem(8, ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2], false).total;
+  if (ctx->opt.real == MLS_F64) return 0;   // the double-precision spread uses no shared memory
   return (size_t)SpreadSmem(4, ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2], spread_vec(ctx)).total;
 }
 
@@ -461,7 +437,7 @@ cudaError_t spread_configure(mls_ctx* ctx) {
   if (ei != cudaSuccess) return ei;
   const int smem = (int)spread_smem_bytes(ctx);
   const int lx = ctx->tiles.l[0], ly = ctx->tiles.l[1], lz = ctx->tiles.l[2];
-  if (ctx->opt.real == MLS_F64) return configure_kernel(ctx, k_spread_f64, smem);
+  if (ctx->opt.real == MLS_F64) return cudaSuccess;
   const bool bf = ctx->opt.field == MLS_BF16;
   if (spread_vec(ctx)) {
     // The scalar variant also runs when f is not aligned for the vector reductions (same layout size or smaller).
@@ -510,9 +486,9 @@ static cudaError_t launch_spread_one(const mls_ctx* ctx, const mls_transfer* T, 
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s) {
   if (T->M == 0) return cudaSuccess;
   if (ctx->opt.real == MLS_F64)
-    k_spread_f64<<<ctx->spread_grid, kSpreadThreads, spread_smem_bytes(ctx), s>>>(
-        dims_of(ctx), ctx->tiles, (const double*)T->phi, (const double*)T->c, T->home, T->perm, T->items,
-        T->n_items, T->offsets, T->counts, T->M, T->cap, (const double*)F, (double*)f);
+    k_spread_f64<<<(unsigned)((T->M + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        dims_of(ctx), (const double*)T->phi, (const double*)T->c, T->home, T->perm, T->M, T->cap,
+        (const double*)F, (double*)f);
   else if (ctx->opt.field == MLS_BF16)
     return spread_vec_aligned(ctx, f) ? launch_spread_one<__nv_bfloat16, true>(ctx, T, F, f, s)
                                       : launch_spread_one<__nv_bfloat16, false>(ctx, T, F, f, s);
