@@ -306,7 +306,8 @@ cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* 
                                cudaStream_t s) {
   const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
   if (ctx->opt.real == MLS_F64)
-    k_build_exact<double><<<grid, kBlock, 0, s>>>(make_args<double>(ctx, T, x, area, M));
+    k_build_exact<double><<<(unsigned)((M + kBlockF64 - 1) / kBlockF64), kBlockF64, 0, s>>>(
+        make_args<double>(ctx, T, x, area, M));
   else {
     const BuildArgs<float> a = make_args<float>(ctx, T, x, area, M);
     k_build_exact<float><<<grid, kBlock, 0, s>>>(a);
@@ -320,7 +321,8 @@ cudaError_t launch_build_fast(const mls_ctx* ctx, mls_transfer* T, const void* x
                               cudaStream_t s) {
   const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
   if (ctx->opt.real == MLS_F64)
-    k_build_fast<double><<<grid, kBlock, 0, s>>>(make_args<double>(ctx, T, x, area, M));
+    k_build_fast<double><<<(unsigned)((M + kBlockF64 - 1) / kBlockF64), kBlockF64, 0, s>>>(
+        make_args<double>(ctx, T, x, area, M));
   else if (ctx->fast_smem_grid > 0 && ctx->n_classes == 1) {
     const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
     const int vec4 = (int)(S3 * kTableRow / 4);

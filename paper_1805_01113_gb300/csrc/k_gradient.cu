@@ -150,8 +150,8 @@ cudaError_t launch_interp_gradient(const mls_ctx* ctx, const mls_transfer* T, co
   const Dims D = dims_of(ctx);
   const double ie2 = 1.0 / (ctx->opt.eps * ctx->opt.eps);
   if (ctx->opt.real == MLS_F64)
-    k_interp_gradient<double, double><<<grid, kBlock, 0, s>>>(D, device_grid<double>(ctx), (const double*)x, T->home,
-                                                              T->perm, T->M, ie2, 0, (const double*)u, (double*)G);
+    k_interp_gradient<double, double><<<(unsigned)((T->M + kBlockF64 - 1) / kBlockF64), kBlockF64, 0, s>>>(
+        D, device_grid<double>(ctx), (const double*)x, T->home, T->perm, T->M, ie2, 0, (const double*)u, (double*)G);
   else if (ctx->opt.field == MLS_F32)
     k_interp_gradient<float, float><<<grid, kBlock, 0, s>>>(D, device_grid<float>(ctx), (const float*)x, T->home,
                                                             T->perm, T->M, (float)ie2, ctx->opt.refine,

@@ -83,6 +83,8 @@ namespace mls {
 constexpr int kScanTile = 4096;       // bins per scan tile
 constexpr int kScanMaxTiles = 8192;   // bins <= 32 Mi
 constexpr int kBlock = 256;           // threads per block of the per-marker kernels
+constexpr int kBlockF64 = 64;         // the same for the double-precision builds and gradient (FP64-bound:
+                                      // small workloads should spread over many SMs)
 constexpr int kSpreadThreads = 128;   // threads per block of the spreading kernel
 constexpr int kTableRow = 28;         // fast-MLS table row: 27 shape-function values + 1 pad (16-byte rows)
 constexpr int kInterpThreads = 128;   // threads per block of the tile-organised interpolation
