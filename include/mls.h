@@ -357,6 +357,29 @@ int mls_surrogate_forward(mls_ctx* ctx, const float* X, int32_t B, int32_t mode,
 int mls_surrogate_loss_grad(mls_ctx* ctx, const float* X, const float* T, int32_t B, float* grad, float* loss,
                             void* stream);
 
+/* ---- checkpoint / resume ------------------------------------------------
+ * The context's marker-independent state: the fast-MLS table (Section 2,
+ * Fig. 1b/1c; real[n_classes][n_sub^3][27] shape functions at the sub-Eulerian
+ * points) when an MLS_FAST build or mls_fast_table has made it, and the
+ * surrogate's float32 parameters when trained or set.  The file holds a
+ * versioned header, a 64-bit key over the grid (n, periodic, every face), eps,
+ * n_sub and the real precision, the present blocks, and a trailing checksum.
+ *
+ * mls_save: synchronises the device, writes `path` (host file name) through a
+ * temporary "<path>.partial" that is renamed into place.  A context with
+ * neither block writes a header-only file.  MLS_ERR_INVALID_ARG when the file
+ * cannot be written; CUDA errors as MLS_ERR_CUDA.
+ *
+ * mls_load: reads and validates the whole file before changing the context;
+ * then allocates the table if absent, copies it in (after a device
+ * synchronise, so launches still using the old table finish first), and sets
+ * the surrogate parameters as mls_surrogate_params(set = 1) does.
+ * MLS_ERR_INVALID_ARG for a missing or unreadable file, a bad magic, version,
+ * checksum or layout, or a key that differs from this context's (another grid
+ * or option set); the context is then unchanged.  Both are synchronous. */
+int mls_save(mls_ctx* ctx, const char* path);
+int mls_load(mls_ctx* ctx, const char* path);
+
 /* Per-kernel CUDA-event timing on the launching stream (off by default).
  * mls_timing_read synchronises the device, returns up to `max` accumulated
  * records in `out`, their count in `n`, and resets the accumulators. */

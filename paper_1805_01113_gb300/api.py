@@ -5,6 +5,7 @@ extraction); every step of the path runs in libmls_gb300.so kernels.
 """
 
 import ctypes as C
+import os
 
 import torch
 
@@ -246,6 +247,15 @@ class Context:
         row = B.MLS_TABLE_ROW
         return torch.as_tensor(_DeviceArray(p.value, (nc.value, s3, 27), self.real_t,
                                             (s3 * row * es, row * es, es)), device=dev)
+
+    # -- checkpoint -----------------------------------------------------------
+    def save(self, path):
+        """Write the fast-MLS table (if built) and surrogate parameters (if any) to `path` (mls_save)."""
+        B.check(self.lib.mls_save(self.handle, os.fsencode(path)), "mls_save")
+
+    def load(self, path):
+        """Install a checkpoint written by save() for the same grid and options (mls_load)."""
+        B.check(self.lib.mls_load(self.handle, os.fsencode(path)), "mls_load")
 
     # -- learned surrogate ----------------------------------------------------
     def train_surrogate(self, stream=None, **kw):

@@ -90,6 +90,8 @@ SIGNATURES = {
     "mls_train_options_default": (C.c_int, [C.POINTER(mls_train_options)]),
     "mls_surrogate_train": (C.c_int, [C.c_void_p, C.POINTER(mls_train_options), C.c_void_p, C.POINTER(C.c_double)]),
     "mls_surrogate_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32]),
+    "mls_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "mls_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mls_surrogate_samples": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
                                         C.c_void_p]),
     "mls_surrogate_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),

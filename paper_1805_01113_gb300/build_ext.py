@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libmls_gb300.so")
 SOURCES = ["mls_api.cu", "k_prep_sort.cu", "k_build.cu", "k_transfer.cu", "k_force.cu", "k_collision.cu", "k_refine.cu",
            "k_gradient.cu",
            "mls_noalloc.cu",
-           "k_mlp.cu", "mls_surrogate_api.cu"]
+           "k_mlp.cu", "mls_surrogate_api.cu", "mls_checkpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

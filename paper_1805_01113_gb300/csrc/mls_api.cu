@@ -81,6 +81,28 @@ void timer_end(mls_ctx* ctx, int slot, cudaStream_t s) {
   cudaEventRecord(ctx->events[slot].stop, s);
 }
 
+int fast_table_layout(mls_ctx* ctx) {
+  int axis = -1, nonuni = 0;
+  for (int d = 0; d < 3; ++d)
+    if (!ctx->uniform[d]) {
+      axis = d;
+      ++nonuni;
+    }
+  if (nonuni > 1) {
+    set_error("fast-MLS tables need at most one non-uniform axis");
+    return MLS_ERR_UNSUPPORTED;
+  }
+  ctx->class_axis = axis;
+  ctx->n_classes = axis < 0 ? 1 : ctx->n[axis];
+  return MLS_OK;
+}
+
+size_t fast_table_bytes(const mls_ctx* ctx) {
+  const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
+  const size_t rs = ctx->opt.real == MLS_F64 ? sizeof(double) : sizeof(float);
+  return (size_t)ctx->n_classes * S3 * kTableRow * rs;
+}
+
 }  // namespace mls
 
 using namespace mls;
@@ -344,21 +366,9 @@ int mls_refine_markers(mls_ctx* ctx, const void* vertices, int64_t n_vertices, c
 
 static int ensure_table(mls_ctx* ctx, cudaStream_t s) {
   if (ctx->table) return MLS_OK;
-  int axis = -1, nonuni = 0;
-  for (int d = 0; d < 3; ++d)
-    if (!ctx->uniform[d]) {
-      axis = d;
-      ++nonuni;
-    }
-  if (nonuni > 1) {
-    set_error("fast-MLS tables need at most one non-uniform axis");
-    return MLS_ERR_UNSUPPORTED;
-  }
-  ctx->class_axis = axis;
-  ctx->n_classes = axis < 0 ? 1 : ctx->n[axis];
-  const int64_t S3 = (int64_t)ctx->opt.n_sub * ctx->opt.n_sub * ctx->opt.n_sub;
-  const size_t rs = ctx->opt.real == MLS_F64 ? sizeof(double) : sizeof(float);
-  cudaError_t e = cudaMalloc(&ctx->table, (size_t)ctx->n_classes * S3 * kTableRow * rs);
+  int rc = fast_table_layout(ctx);
+  if (rc != MLS_OK) return rc;
+  cudaError_t e = cudaMalloc(&ctx->table, fast_table_bytes(ctx));
   if (e != cudaSuccess) {
     ctx->table = nullptr;
     return cuda_fail(e, "fast-MLS table allocation");

@@ -105,6 +105,11 @@ inline cudaError_t raise_smem_limit(const void* kernel, int bytes) {
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Fast-MLS table shape: sets class_axis and n_classes (MLS_ERR_UNSUPPORTED for
+// more than one non-uniform axis); bytes of the table for that shape.
+int fast_table_layout(mls_ctx* ctx);
+size_t fast_table_bytes(const mls_ctx* ctx);
+
 // Timing helpers (no-ops unless ctx->timing).
 int timer_begin(mls_ctx* ctx, const char* name, cudaStream_t s);
 void timer_end(mls_ctx* ctx, int slot, cudaStream_t s);
