@@ -110,7 +110,8 @@ int cuda_fail(cudaError_t e, const char* what);
 int fast_table_layout(mls_ctx* ctx);
 size_t fast_table_bytes(const mls_ctx* ctx);
 
-// Timing helpers (no-ops unless ctx->timing).
+// Phase helpers: every call opens and closes an NVTX range named after the
+// phase; CUDA events are recorded only when ctx->timing is on.
 int timer_begin(mls_ctx* ctx, const char* name, cudaStream_t s);
 void timer_end(mls_ctx* ctx, int slot, cudaStream_t s);
 
