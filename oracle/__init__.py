@@ -21,6 +21,7 @@ from .mls import (
     locate,
     support,
     gaussian_weight,
+    basis_values,
     shape_exact,
     shape_exact_absolute_basis,
     shape_exact_gradient,
@@ -37,7 +38,7 @@ from .mls import (
 
 __all__ = [
     "collision", "mlp", "refine", "Grid", "marker_prep", "locate", "support", "gaussian_weight",
-    "shape_exact", "shape_exact_absolute_basis", "shape_exact_gradient", "interpolate_gradient", "subnode_offsets", "fast_table",
+    "basis_values", "shape_exact", "shape_exact_absolute_basis", "shape_exact_gradient", "interpolate_gradient", "subnode_offsets", "fast_table",
     "shape_fast", "forcing_scale", "interpolate", "spread", "SparseField",
     "direct_forcing",
 ]

@@ -5,7 +5,8 @@ imports, links or runs this file.
 
 Notation follows Section 2 of the paper: a Lagrangian marker l at x_l, its
 N_e = 27 Eulerian support nodes x_k (the centres of the home cell and of its
-3x3x3 neighbourhood, Fig. 1a), the linear basis p = [1, x, y, z] (m = 4), the
+3x3x3 neighbourhood, Fig. 1a), the linear basis p = [1, x, y, z] (m = 4; the
+quadratic m = 10 as an option), the
 weight W(x_l - x_k), the moment matrix A (Eq. 3), the matrix B (Eq. 4), the
 shape functions Phi^T = p^T(x_l) A^-1 B (Eq. 6), interpolation U = Phi^T u,
 spreading f_k = sum_l c_l phi_k^l F_l with c_l from Eq. 8, and fast-MLS
@@ -165,12 +166,31 @@ class Transfer:
     sup: Support
 
 
-def shape_exact(grid, x, eps=1.0, home=None):
+def basis_values(xi, m=4):
+    """Basis vector p of Section 2 (text after Eq. 2) at the points xi (3, ...).
+
+    The terms come from Pascal's pyramid: m = 4 is the linear basis
+    [1, x, y, z] the paper uses; m = 10 adds the six degree-2 terms
+    [x^2, y^2, z^2, xy, yz, zx] (the paper allows any m; fast-MLS does not
+    depend on it).  Returns an array of shape xi.shape[1:] + (m,).
+    """
+    if m not in (4, 10):
+        raise ValueError("basis size m must be 4 or 10")
+    x, y, z = xi[0], xi[1], xi[2]
+    cols = [np.ones_like(x), x, y, z]
+    if m == 10:
+        cols += [x * x, y * y, z * z, x * y, y * z, z * x]
+    return np.stack(cols, axis=-1)
+
+
+def shape_exact(grid, x, eps=1.0, home=None, basis=4):
     """Exact-MLS shape functions, Eqs. 3, 4 and 6.
 
     The basis is written in marker-centred, home-width-scaled coordinates,
-    p~(x) = [1, (x - x_l)/Delta^home], an invertible affine change of the
-    paper's p = [1, x, y, z] that leaves Phi unchanged (p~(x_l) = e_0).
+    p~(x) = p((x - x_l)/Delta^home), an invertible affine change of the
+    paper's coordinates that maps the space spanned by p (linear, m = 4, or
+    quadratic, m = 10; see basis_values) onto itself and so leaves Phi
+    unchanged, with p~(x_l) = e_0.
     A(x_l) = sum_k W_k p~(x_k) p~(x_k)^T (Eq. 3), B = [W_k p~(x_k)] (Eq. 4),
     Phi^T = p~(x_l)^T A^-1 B (Eq. 6), solved with a library dense solve.
     """
@@ -178,16 +198,15 @@ def shape_exact(grid, x, eps=1.0, home=None):
     sup = support(grid, x, home)
     W = gaussian_weight(x, sup, eps)                       # (M, 27)
     M = x.shape[1]
-    P = np.ones((M, 27, 4))
-    for d in range(3):
-        P[:, :, d + 1] = (sup.pos[d] - x[d][:, None]) / sup.hwidth[d][:, None]
+    xi = np.stack([(sup.pos[d] - x[d][:, None]) / sup.hwidth[d][:, None] for d in range(3)])
+    P = basis_values(xi, basis)                            # (M, 27, m)
     A = np.einsum("mk,mki,mkj->mij", W, P, P)              # Eq. 3
-    B = np.transpose(W[:, :, None] * P, (0, 2, 1))         # Eq. 4, (M, 4, 27)
+    B = np.transpose(W[:, :, None] * P, (0, 2, 1))         # Eq. 4, (M, m, 27)
     good = sup.ok.copy()
     phi = np.zeros((M, 27))
     if np.any(good):
         X = np.linalg.solve(A[good], B[good])              # A^-1 B
-        pl = np.array([1.0, 0.0, 0.0, 0.0])                # p~(x_l)
+        pl = basis_values(np.zeros(3), basis)              # p~(x_l) = e_0
         phi[good] = np.einsum("i,mik->mk", pl, X)          # Eq. 6
     return Transfer(phi, sup)
 
@@ -279,7 +298,7 @@ def subnode_offsets(n_sub):
     return -0.5 + np.arange(n_sub, dtype=np.float64) / (n_sub - 1)
 
 
-def fast_table(grid, home, n_sub=9, eps=1.0):
+def fast_table(grid, home, n_sub=9, eps=1.0, basis=4):
     """Exact shape functions at the n^3 sub-Eulerian nodes of one home cell (Section 2, Fig. 1b/1c).
 
     ``home`` is a length-3 cell index.  Returns (n^3, 27) in sub-node order
@@ -293,7 +312,7 @@ def fast_table(grid, home, n_sub=9, eps=1.0):
     for d in range(3):
         X[d] = grid.faces[d][home[d]] + (rel[d] + 0.5) * grid.widths[d][home[d]]
     H = np.repeat(np.asarray(home, dtype=np.int64)[:, None], n_sub ** 3, axis=1)
-    return shape_exact(grid, X, eps, home=H).phi
+    return shape_exact(grid, X, eps, home=H, basis=basis).phi
 
 
 def _table_key(grid, home):
@@ -302,7 +321,7 @@ def _table_key(grid, home):
     return tuple(int(home[d]) if not grid.uniform_axis(d) else grid.n[d] // 2 for d in range(3))
 
 
-def shape_fast(grid, x, eps=1.0, n_sub=9, home=None, subcell=None, tables=None):
+def shape_fast(grid, x, eps=1.0, n_sub=9, home=None, subcell=None, tables=None, basis=4):
     """Fast-MLS shape functions, Eqs. 9-10.
 
     The marker's offset in its home cell, t in [-1/2, 1/2)^3, selects the
@@ -314,7 +333,8 @@ def shape_fast(grid, x, eps=1.0, n_sub=9, home=None, subcell=None, tables=None):
 
     ``subcell`` (3, M) optionally forces the sub-cell (used to compare with a
     single-precision caller that resolved a sub-cell face the other way).
-    ``tables`` is an optional dict cache shared between calls.
+    ``tables`` is an optional dict cache shared between calls.  ``basis``
+    (m = 4 or 10) is the basis of the tabulated exact shape functions.
     """
     x = np.asarray(x, dtype=np.float64)
     sup = support(grid, x, home)
@@ -334,9 +354,9 @@ def shape_fast(grid, x, eps=1.0, n_sub=9, home=None, subcell=None, tables=None):
     corners = [(cx, cy, cz) for cz in (0, 1) for cy in (0, 1) for cx in (0, 1)]
     for m in np.nonzero(sup.ok)[0]:
         key = _table_key(grid, sup.home[:, m])
-        if key not in tables:
-            tables[key] = fast_table(grid, key, n_sub, eps)
-        T = tables[key]
+        if (key, basis) not in tables:
+            tables[(key, basis)] = fast_table(grid, key, n_sub, eps, basis)
+        T = tables[(key, basis)]
         d2 = np.array([sum(((lam[d, m] - c[d]) / nm1) ** 2 for d in range(3)) for c in corners])
         nodes = [((s[2, m] + c[2]) * n_sub + (s[1, m] + c[1])) * n_sub + (s[0, m] + c[0]) for c in corners]
         if np.min(d2) < 1e-24:

@@ -27,15 +27,16 @@ def _markers_in_cell(grid, home, t):
 
 @pytest.mark.parametrize("grid", [_grid_uniform(), _grid_stretched()], ids=["uniform", "stretched"])
 @pytest.mark.parametrize("n_sub", [3, 5, 9])
-def test_exact_at_subnodes(grid, n_sub):
-    """A marker on an interior sub-node gets that node's tabulated exact phi (d_i = 0)."""
+@pytest.mark.parametrize("basis", [4, 10])
+def test_exact_at_subnodes(grid, n_sub, basis):
+    """A marker on an interior sub-node gets that node's tabulated exact phi (d_i = 0), for either basis."""
     home = (5, 6, 9)
     off = oracle.subnode_offsets(n_sub)
     sel = RNG.integers(1, n_sub - 1, size=(3, 20))       # interior sub-nodes (faces belong to two cells)
     t = off[sel]
     x = _markers_in_cell(grid, home, t)
-    f = oracle.shape_fast(grid, x, 1.0, n_sub)
-    e = oracle.shape_exact(grid, x, 1.0)
+    f = oracle.shape_fast(grid, x, 1.0, n_sub, basis=basis)
+    e = oracle.shape_exact(grid, x, 1.0, basis=basis)
     assert np.max(np.abs(f.phi - e.phi)) < 1e-13
 
 

@@ -109,3 +109,23 @@ def test_missing_area_in_scale_is_caught():
     wrong = h_l / np.sum(tr.phi * w[0] * w[1] * w[2], axis=1)   # A_l dropped from dV_l
     assert np.max(np.abs(oracle.forcing_scale(tr, area) - area / h ** 2)) < 1e-12
     assert np.max(np.abs(wrong - area / h ** 2)) > 1.0
+
+
+def test_quadratic_basis_with_a_wrong_cross_term_is_caught(monkeypatch):
+    """A cross term written as xy where zx belongs still fits data but fails reproduction of zx."""
+    grid = _stretched()
+    x = _random_markers(grid, 30, np.random.default_rng(6))
+    real = om.basis_values
+
+    def garbled(xi, m=4):
+        p = real(xi, m)
+        if m == 10:
+            p = p.copy()
+            p[..., 9] = xi[0] * xi[1] * xi[1]              # a cubic where z*x belongs
+        return p
+
+    monkeypatch.setattr(om, "basis_values", garbled)
+    tr = oracle.shape_exact(grid, x, 1.0, basis=10)
+    rel = [(tr.sup.pos[d] - x[d][:, None]) / tr.sup.hwidth[d][:, None] for d in range(3)]
+    zx = np.sum(tr.phi * rel[2] * rel[0], axis=1)
+    assert np.max(np.abs(zx)) > 1e-3
