@@ -84,9 +84,15 @@ typedef struct {
   int32_t n_sub;         /* fast-MLS sub-Eulerian points per axis (Fig. 1b/1c), 3..33, default 9 */
   int32_t brick_log2[3]; /* spreading tile of 2^b home cells per axis, 1..5 each, default 3 */
   double cond_max;       /* MLS_F32 only: re-solve Eq. 6 in double when cond_1(A) exceeds this; <= 0 disables; default 1e6 */
-  int32_t refine;        /* MLS_F32 only: iterative-refinement steps of the 4x4 solve, 0..2, default 1 */
+  int32_t refine;        /* MLS_F32 only: iterative-refinement steps of the solve, 0..2, default 1 */
   double residual_max;   /* MLS_SURROGATE: linear-reproduction residual above which a marker
                             falls back to exact-MLS, default 1e-4 */
+  int32_t basis;         /* size m of the MLS basis p (Section 2, text after Eq. 2: Pascal's
+                            pyramid): 4 = [1, x, y, z] (the paper's, default) or
+                            10 = [1, x, y, z, x^2, y^2, z^2, xy, yz, zx].  MLS_EXACT and
+                            MLS_FAST (whose table holds exact shape functions) take either;
+                            the surrogate and mls_interpolate_gradient need 4 and return
+                            MLS_ERR_UNSUPPORTED otherwise */
 } mls_options;
 
 /* Device views into a built transfer (borrowed; valid until the next build on
@@ -363,7 +369,8 @@ int mls_surrogate_loss_grad(mls_ctx* ctx, const float* X, const float* T, int32_
  * points) when an MLS_FAST build or mls_fast_table has made it, and the
  * surrogate's float32 parameters when trained or set.  The file holds a
  * versioned header, a 64-bit key over the grid (n, periodic, every face), eps,
- * n_sub and the real precision, the present blocks, and a trailing checksum.
+ * n_sub, the basis size and the real precision, the present blocks, and a
+ * trailing checksum.
  *
  * mls_save: synchronises the device, writes `path` (host file name) through a
  * temporary "<path>.partial" that is renamed into place.  A context with

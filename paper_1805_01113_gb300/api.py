@@ -75,7 +75,7 @@ class Context:
     """One grid + option set (mls_create)."""
 
     def __init__(self, faces, periodic, real="f32", field=None, eps=1.0, n_sub=9, brick_log2=(3, 3, 3),
-                 cond_max=1e6, refine=1, residual_max=1e-4):
+                 cond_max=1e6, refine=1, residual_max=1e-4, basis=4):
         self.lib = B.load()
         field = field or real
         self.real_code, self.real_t = DTYPES[real]
@@ -93,6 +93,7 @@ class Context:
         for d in range(3):
             o.brick_log2[d] = int(brick_log2[d])
         o.cond_max, o.refine, o.residual_max = float(cond_max), int(refine), float(residual_max)
+        o.basis = int(basis)
         self.options = o
         h = C.c_void_p()
         B.check(self.lib.mls_create(C.byref(g), C.byref(o), C.byref(h)), "mls_create")

@@ -37,7 +37,7 @@ class mls_grid(C.Structure):
 class mls_options(C.Structure):
     _fields_ = [("real", C.c_int32), ("field", C.c_int32), ("eps", C.c_double), ("n_sub", C.c_int32),
                 ("brick_log2", C.c_int32 * 3), ("cond_max", C.c_double), ("refine", C.c_int32),
-                ("residual_max", C.c_double)]
+                ("residual_max", C.c_double), ("basis", C.c_int32)]
 
 
 class mls_transfer_arrays(C.Structure):

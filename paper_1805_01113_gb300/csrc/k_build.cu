@@ -76,26 +76,36 @@ __device__ __forceinline__ void marker_finish(const BuildArgs<R>& a, int64_t j, 
 // Exact-MLS build (Eqs. 3-6, 8): phi is written node by node as it is formed.
 // A single-precision solve that is ill-conditioned (cond_1(A) > cond_max) or
 // not numerically SPD queues the marker for k_build_exact_redo instead.
-template <typename R>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact(BuildArgs<R> a) {
+// MB is the basis size: 4 (linear, the paper's) or kQuad (quadratic).
+template <typename R, int MB>
+__global__ void __launch_bounds__(kBlock, MB == 4 && sizeof(R) == 4 ? 4 : 1) k_build_exact(BuildArgs<R> a) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.M) return;
   int h[3];
   R p[3], ar;
   AxisNodes<R> s[3];
   if (!marker_setup(a, j, h, p, s, ar)) return;
-  R w[3][3], y[4];
+  R w[3][3], y[MB];
   R cond = R(0);
   const bool want_cond = sizeof(R) == 4 && a.want_cond;
-  bool good = exact_solve<R>(s, a.inv_eps2, a.refine, w, y, want_cond ? &cond : nullptr);
+  bool good = exact_solve_m<MB>(s, a.inv_eps2, a.refine, w, y, want_cond ? &cond : nullptr);
   if (sizeof(R) == 4 && (!good || (want_cond && (float)cond > a.cond_max_f))) {
     a.redo[atomicAdd(&a.status[2], 1ULL)] = (int32_t)j;
     return;
   }
   R c = R(0);
   if (good) {
-    c = exact_scale(s, w, y, ar);
-    exact_emit(s, w, y, [&](int q, int b, int cc, R v) { a.phi[(9 * cc + 3 * b + q) * a.cap + j] = v; });
+    if constexpr (MB == 4) {
+      c = exact_scale(s, w, y, ar);
+      exact_emit(s, w, y, [&](int q, int b, int cc, R v) { a.phi[(9 * cc + 3 * b + q) * a.cap + j] = v; });
+    } else {
+      ScaleSums<R> sums;
+      exact_emit_m<MB>(s, w, y, [&](int q, int b, int cc, R v) {
+        a.phi[(9 * cc + 3 * b + q) * a.cap + j] = v;
+        sums.add(s, q, b, cc, v);
+      });
+      c = sums.vol != R(0) ? sums.scale(s, ar) : R(0);
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = R(0);
@@ -106,6 +116,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact(
 
 // The queued single-precision markers, solved in double and rounded
 // (grid-stride over the queue that k_build_exact filled).
+template <int MB>
 __global__ void __launch_bounds__(kBlock) k_build_exact_redo(BuildArgs<float> a) {
   const unsigned long long n = a.status[2];
   for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
@@ -118,11 +129,11 @@ __global__ void __launch_bounds__(kBlock) k_build_exact_redo(BuildArgs<float> a)
     AxisNodes<double> sd[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) sd[d] = axis_nodes(a.gd.ax[d], h[d], (double)p[d]);
-    double wd[3][3], yd[4];
-    const bool good = exact_solve<double>(sd, a.inv_eps2_d, 0, wd, yd, nullptr);
+    double wd[3][3], yd[MB];
+    const bool good = exact_solve_m<MB>(sd, a.inv_eps2_d, 0, wd, yd, (double*)nullptr);
     ScaleSums<float> sums;
     if (good) {
-      exact_emit(sd, wd, yd, [&](int qq, int b, int c, double v) {
+      exact_emit_m<MB>(sd, wd, yd, [&](int qq, int b, int c, double v) {
         a.phi[(9 * c + 3 * b + qq) * a.cap + j] = (float)v;
         sums.add(s, qq, b, c, (float)v);
       });
@@ -243,7 +254,7 @@ __global__ void __launch_bounds__(kFastSmemThreads, 2) k_build_fast_smem(BuildAr
 // (faces included) of one home cell per class, computed in double and
 // rounded to R.  A class is the home index along the single non-uniform axis;
 // uniform axes have unit neighbour/home width ratios.
-template <typename R>
+template <typename R, int MB>
 __global__ void k_fast_table(Grid<double> gd, int class_axis, int64_t n_classes, int n_sub, double inv_eps2,
                              R* __restrict__ table) {
   const int64_t S3 = (int64_t)n_sub * n_sub * n_sub;
@@ -267,7 +278,7 @@ __global__ void k_fast_table(Grid<double> gd, int class_axis, int64_t n_classes,
     }
   }
   double phi[27];
-  if (!shape_exact<double>(nd, inv_eps2, 0, phi, nullptr)) {
+  if (!shape_exact<double, MB>(nd, inv_eps2, 0, phi, nullptr)) {
     for (int k = 0; k < 27; ++k) phi[k] = 0.0;
   }
   for (int k = 0; k < 27; ++k) table[idx * kTableRow + k] = (R)phi[k];
@@ -302,18 +313,27 @@ static BuildArgs<R> make_args(const mls_ctx* ctx, mls_transfer* T, const void* x
   return a;
 }
 
-cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
-                               cudaStream_t s) {
+template <int MB>
+static void launch_build_exact_m(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                                 cudaStream_t s) {
   const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
   if (ctx->opt.real == MLS_F64)
-    k_build_exact<double><<<(unsigned)((M + kBlockF64 - 1) / kBlockF64), kBlockF64, 0, s>>>(
+    k_build_exact<double, MB><<<(unsigned)((M + kBlockF64 - 1) / kBlockF64), kBlockF64, 0, s>>>(
         make_args<double>(ctx, T, x, area, M));
   else {
     const BuildArgs<float> a = make_args<float>(ctx, T, x, area, M);
-    k_build_exact<float><<<grid, kBlock, 0, s>>>(a);
+    k_build_exact<float, MB><<<grid, kBlock, 0, s>>>(a);
     const unsigned redo_grid = (unsigned)std::min<int64_t>(grid, 4 * 152);
-    k_build_exact_redo<<<redo_grid, kBlock, 0, s>>>(a);
+    k_build_exact_redo<MB><<<redo_grid, kBlock, 0, s>>>(a);
   }
+}
+
+cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                               cudaStream_t s) {
+  if (ctx->opt.basis == kQuad)
+    launch_build_exact_m<kQuad>(ctx, T, x, area, M, s);
+  else
+    launch_build_exact_m<4>(ctx, T, x, area, M, s);
   return cudaGetLastError();
 }
 
@@ -362,12 +382,21 @@ cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s) {
   const int64_t total = ctx->n_classes * S3;
   const unsigned grid = (unsigned)((total + 127) / 128);
   const double inv_eps2 = 1.0 / (ctx->opt.eps * ctx->opt.eps);
-  if (ctx->opt.real == MLS_F64)
-    k_fast_table<double><<<grid, 128, 0, s>>>(device_grid<double>(ctx), ctx->class_axis, ctx->n_classes,
-                                              ctx->opt.n_sub, inv_eps2, (double*)ctx->table);
-  else
-    k_fast_table<float><<<grid, 128, 0, s>>>(device_grid<double>(ctx), ctx->class_axis, ctx->n_classes,
-                                             ctx->opt.n_sub, inv_eps2, (float*)ctx->table);
+  const Grid<double> gd = device_grid<double>(ctx);
+  const bool quad = ctx->opt.basis == kQuad;
+  if (ctx->opt.real == MLS_F64) {
+    double* t = (double*)ctx->table;
+    if (quad)
+      k_fast_table<double, kQuad><<<grid, 128, 0, s>>>(gd, ctx->class_axis, ctx->n_classes, ctx->opt.n_sub, inv_eps2, t);
+    else
+      k_fast_table<double, 4><<<grid, 128, 0, s>>>(gd, ctx->class_axis, ctx->n_classes, ctx->opt.n_sub, inv_eps2, t);
+  } else {
+    float* t = (float*)ctx->table;
+    if (quad)
+      k_fast_table<float, kQuad><<<grid, 128, 0, s>>>(gd, ctx->class_axis, ctx->n_classes, ctx->opt.n_sub, inv_eps2, t);
+    else
+      k_fast_table<float, 4><<<grid, 128, 0, s>>>(gd, ctx->class_axis, ctx->n_classes, ctx->opt.n_sub, inv_eps2, t);
+  }
   return cudaGetLastError();
 }
 

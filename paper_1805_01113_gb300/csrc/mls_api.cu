@@ -139,6 +139,7 @@ int mls_options_default(mls_options* opt) {
   opt->cond_max = 1e6;
   opt->refine = 1;
   opt->residual_max = 1e-4;
+  opt->basis = 4;
   return MLS_OK;
 }
 
@@ -175,6 +176,7 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
   if (opt.n_sub < 3 || opt.n_sub > 33) return invalid("mls_create: n_sub must be in [3, 33]");
   if (opt.refine < 0 || opt.refine > 2) return invalid("mls_create: refine must be 0, 1 or 2");
   if (!(opt.residual_max > 0.0)) return invalid("mls_create: residual_max must be positive");
+  if (opt.basis != 4 && opt.basis != kQuad) return invalid("mls_create: basis must be 4 or 10");
   for (int d = 0; d < 3; ++d)
     if (opt.brick_log2[d] < 1 || opt.brick_log2[d] > 5) return invalid("mls_create: brick_log2 must be in [1, 5]");
   int64_t cells = 1;
@@ -402,8 +404,9 @@ int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void*
   }
   if (method != MLS_EXACT && method != MLS_FAST && method != MLS_SURROGATE)
     return invalid("mls_build_transfer: unknown method");
-  if (method == MLS_SURROGATE && (!ctx->mlp_pack || ctx->opt.real != MLS_F32)) {
-    set_error("mls_build_transfer: the surrogate needs a single-precision context with trained or loaded parameters");
+  if (method == MLS_SURROGATE && (!ctx->mlp_pack || ctx->opt.real != MLS_F32 || ctx->opt.basis != 4)) {
+    set_error("mls_build_transfer: the surrogate needs a single-precision, linear-basis context with trained or "
+              "loaded parameters");
     return MLS_ERR_UNSUPPORTED;
   }
   if (M > 0 && (!x || !area)) return invalid("mls_build_transfer: NULL marker arrays");
@@ -459,6 +462,10 @@ int mls_interpolate_gradient(mls_ctx* ctx, const mls_transfer* T, const void* x,
   if (!ctx || !T) return invalid("mls_interpolate_gradient: NULL handle");
   if (T->ctx != ctx) return invalid("mls_interpolate_gradient: transfer belongs to another context");
   if (T->M > 0 && (!x || !u || !G)) return invalid("mls_interpolate_gradient: NULL positions, field or output");
+  if (ctx->opt.basis != 4) {
+    set_error("mls_interpolate_gradient: derivative shape functions are implemented for the linear basis only");
+    return MLS_ERR_UNSUPPORTED;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int slot = timer_begin(ctx, "interp_gradient", s);
   cudaError_t e = launch_interp_gradient(ctx, T, x, u, G, s);

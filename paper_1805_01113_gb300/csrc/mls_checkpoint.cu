@@ -40,8 +40,8 @@ struct Fnv {
 };
 
 // Everything the table and the surrogate are a function of: the grid (face
-// coordinates, periodicity), the Gaussian width eps, the sub-point count and
-// the arithmetic precision.
+// coordinates, periodicity), the Gaussian width eps, the sub-point count, the
+// basis size and the arithmetic precision.
 uint64_t context_key(const mls_ctx* ctx) {
   Fnv f;
   for (int d = 0; d < 3; ++d) {
@@ -50,6 +50,7 @@ uint64_t context_key(const mls_ctx* ctx) {
   }
   f.put<int32_t>(ctx->opt.real);
   f.put<int32_t>(ctx->opt.n_sub);
+  f.put<int32_t>(ctx->opt.basis);
   f.put<double>(ctx->opt.eps);
   for (int d = 0; d < 3; ++d) f.add(ctx->faces_host[d].data(), ctx->faces_host[d].size() * sizeof(double));
   return f.h;

@@ -378,13 +378,193 @@ __device__ __forceinline__ R exact_scale(const AxisNodes<R> s[3], const R w[3][3
   return vol != R(0) ? (area * ((hx + hy + hz) / R(3))) / vol : R(0);
 }
 
-// All 27 exact shape functions (table path).
+// ---- quadratic basis (m = 10) ------------------------------------------------
+// Section 2 takes the basis from Pascal's pyramid and leaves m free; the
+// quadratic option is p = [1, xi_x, xi_y, xi_z, xi_x^2, xi_y^2, xi_z^2,
+// xi_x xi_y, xi_y xi_z, xi_z xi_x] in the same marker-centred, home-width-scaled
+// coordinates (an affine change that maps the quadratic space onto itself, so
+// Phi is unchanged and p(x_l) = e_0).  quad_exp(i, d) is the exponent of axis d
+// in term i; with the tensor-product weight every entry of A is a product of
+// three per-axis moments, A_ij = prod_d S_{e_i,d + e_j,d}[d], S_m = sum_a w_a xi_a^m.
+constexpr int kQuad = 10;
+constexpr int kQuadPacked = kQuad * (kQuad + 1) / 2;
+
+__host__ __device__ constexpr int quad_exp(int i, int d) {
+  return i == 0   ? 0
+         : i <= 3 ? (i - 1 == d ? 1 : 0)
+         : i <= 6 ? (i - 4 == d ? 2 : 0)
+         : i == 7 ? (d == 0 || d == 1 ? 1 : 0)
+         : i == 8 ? (d == 1 || d == 2 ? 1 : 0)
+                  : (d == 2 || d == 0 ? 1 : 0);
+}
+
+__host__ __device__ constexpr int packed(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+
 template <typename R>
+__device__ __forceinline__ R quad_entry(const R S[3][5], int i, int j) {
+  return S[0][quad_exp(i, 0) + quad_exp(j, 0)] * S[1][quad_exp(i, 1) + quad_exp(j, 1)] *
+         S[2][quad_exp(i, 2) + quad_exp(j, 2)];
+}
+
+// In-place Cholesky of the packed lower triangle (row by row, i >= j); the
+// diagonal slots end up holding 1/L_ii.  Returns false unless every pivot is
+// positive.
+template <typename R>
+__device__ __forceinline__ bool quad_factor(R L[kQuadPacked]) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < kQuad; ++j) {
+    R d = L[packed(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= L[packed(j, k)] * L[packed(j, k)];
+    ok = ok && d > R(0);
+    const R inv = inv_sqrt(d);
+    L[packed(j, j)] = inv;
+#pragma unroll
+    for (int i = j + 1; i < kQuad; ++i) {
+      R v = L[packed(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= L[packed(i, k)] * L[packed(j, k)];
+      L[packed(i, j)] = v * inv;
+    }
+  }
+  return ok;
+}
+
+template <typename R>
+__device__ __forceinline__ void quad_solve(const R L[kQuadPacked], const R b[kQuad], R y[kQuad]) {
+  R z[kQuad];
+#pragma unroll
+  for (int i = 0; i < kQuad; ++i) {
+    R v = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) v -= L[packed(i, k)] * z[k];
+    z[i] = v * L[packed(i, i)];
+  }
+#pragma unroll
+  for (int i = kQuad - 1; i >= 0; --i) {
+    R v = z[i];
+#pragma unroll
+    for (int k = i + 1; k < kQuad; ++k) v -= L[packed(k, i)] * y[k];
+    y[i] = v * L[packed(i, i)];
+  }
+}
+
+// Exact-MLS solve with the quadratic basis: as exact_solve, A y = e_0 with
+// `refine` residual corrections (A re-formed from the moments), cond_1(A)
+// from the column sums of A and of A^-1 (columns of A^-1 by ten solves).
+template <typename R>
+__device__ __forceinline__ bool exact_solve_quad(const AxisNodes<R> s[3], R inv_eps2, int refine, R w[3][3],
+                                                 R y[kQuad], R* cond) {
+  R S[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) S[d][m] = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const R xi = s[d].xi[a];
+      const R wa = dev_exp<R>(-(xi * xi) * inv_eps2);
+      w[d][a] = wa;
+      R pw = wa;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        S[d][m] += pw;
+        pw *= xi;
+      }
+    }
+  }
+  R L[kQuadPacked];
+#pragma unroll
+  for (int i = 0; i < kQuad; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) L[packed(i, j)] = quad_entry(S, i, j);
+  if (!quad_factor(L)) return false;
+  R e0[kQuad];
+#pragma unroll
+  for (int i = 0; i < kQuad; ++i) e0[i] = i == 0 ? R(1) : R(0);
+  quad_solve(L, e0, y);
+  for (int it = 0; it < refine; ++it) {
+    R r[kQuad], dy[kQuad];
+#pragma unroll
+    for (int i = 0; i < kQuad; ++i) {
+      R v = e0[i];
+#pragma unroll
+      for (int j = 0; j < kQuad; ++j) v -= quad_entry(S, i, j) * y[j];
+      r[i] = v;
+    }
+    quad_solve(L, r, dy);
+#pragma unroll
+    for (int i = 0; i < kQuad; ++i) y[i] += dy[i];
+  }
+  if (cond) {
+    R an = R(0), inv_n = R(0);
+#pragma unroll
+    for (int j = 0; j < kQuad; ++j) {
+      R col = R(0), ej[kQuad], xj[kQuad];
+#pragma unroll
+      for (int i = 0; i < kQuad; ++i) {
+        col += fabs(quad_entry(S, i, j));
+        ej[i] = i == j ? R(1) : R(0);
+      }
+      quad_solve(L, ej, xj);
+      R icol = R(0);
+#pragma unroll
+      for (int i = 0; i < kQuad; ++i) icol += fabs(xj[i]);
+      an = fmax(an, col);
+      inv_n = fmax(inv_n, icol);
+    }
+    *cond = an * inv_n;
+  }
+  return true;
+}
+
+// phi_k = W_k (y . p_k) for the quadratic basis, k = 9c + 3b + a: the terms
+// without xi_x are formed once per (b, c), the rest as xi_x (g1 + y4 xi_x).
+template <typename R, typename Sink>
+__device__ __forceinline__ void exact_emit_quad(const AxisNodes<R> s[3], const R w[3][3], const R y[kQuad],
+                                                Sink&& sink) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R wyz = w[1][b] * w[2][c];
+      const R yb = s[1].xi[b], zc = s[2].xi[c];
+      const R g0 = y[0] + y[2] * yb + y[3] * zc + y[5] * (yb * yb) + y[6] * (zc * zc) + y[8] * (yb * zc);
+      const R g1 = y[1] + y[7] * yb + y[9] * zc;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R xa = s[0].xi[a];
+        sink(a, b, c, (w[0][a] * wyz) * (g0 + xa * (g1 + y[4] * xa)));
+      }
+    }
+}
+
+// Basis-size dispatch: MB = 4 (linear) or kQuad (quadratic).
+template <int MB, typename R>
+__device__ __forceinline__ bool exact_solve_m(const AxisNodes<R> s[3], R inv_eps2, int refine, R w[3][3], R y[MB],
+                                              R* cond) {
+  if constexpr (MB == 4)
+    return exact_solve(s, inv_eps2, refine, w, y, cond);
+  else
+    return exact_solve_quad(s, inv_eps2, refine, w, y, cond);
+}
+
+template <int MB, typename R, typename Sink>
+__device__ __forceinline__ void exact_emit_m(const AxisNodes<R> s[3], const R w[3][3], const R y[MB], Sink&& sink) {
+  if constexpr (MB == 4)
+    exact_emit(s, w, y, sink);
+  else
+    exact_emit_quad(s, w, y, sink);
+}
+
+// All 27 exact shape functions (table path).
+template <typename R, int MB = 4>
 __device__ __forceinline__ bool shape_exact(const AxisNodes<R> s[3], R inv_eps2, int refine, R phi[27],
                                             R* cond) {
-  R w[3][3], y[4];
-  if (!exact_solve(s, inv_eps2, refine, w, y, cond)) return false;
-  exact_emit(s, w, y, [&](int a, int b, int c, R v) { phi[9 * c + 3 * b + a] = v; });
+  R w[3][3], y[MB];
+  if (!exact_solve_m<MB>(s, inv_eps2, refine, w, y, cond)) return false;
+  exact_emit_m<MB>(s, w, y, [&](int a, int b, int c, R v) { phi[9 * c + 3 * b + a] = v; });
   return true;
 }
 

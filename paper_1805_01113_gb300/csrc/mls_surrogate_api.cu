@@ -16,6 +16,8 @@ int fail(int code, const std::string& msg) {
 int need_surrogate_grid(mls_ctx* ctx, const char* who) {
   if (ctx->opt.real != MLS_F32)
     return fail(MLS_ERR_UNSUPPORTED, std::string(who) + ": the surrogate runs in single-precision contexts");
+  if (ctx->opt.basis != 4)
+    return fail(MLS_ERR_UNSUPPORTED, std::string(who) + ": the surrogate learns linear-basis shape functions");
   if (surrogate_class_axis(ctx) == -2)
     return fail(MLS_ERR_UNSUPPORTED, std::string(who) + ": the surrogate needs at most one non-uniform axis");
   return MLS_OK;

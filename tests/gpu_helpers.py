@@ -62,10 +62,11 @@ def run_gpu(ctx, x, area, method, u=None, F=None, f=None, T=None):
     return out
 
 
-def run_oracle(grid, x, area, method, u=None, F=None, eps=1.0, n_sub=9):
+def run_oracle(grid, x, area, method, u=None, F=None, eps=1.0, n_sub=9, basis=4):
     x = np.asarray(x, dtype=np.float64)
     area = np.asarray(area, dtype=np.float64)
-    tr = oracle.shape_exact(grid, x, eps) if method == "exact" else oracle.shape_fast(grid, x, eps, n_sub)
+    tr = (oracle.shape_exact(grid, x, eps, basis=basis) if method == "exact"
+          else oracle.shape_fast(grid, x, eps, n_sub, basis=basis))
     # The library also drops markers whose area is not finite (input validation).
     bad = ~np.isfinite(area)
     tr.sup.ok &= ~bad
@@ -78,7 +79,7 @@ def run_oracle(grid, x, area, method, u=None, F=None, eps=1.0, n_sub=9):
     return out
 
 
-def fast_tie_fix(grid, x, phi_gpu, phi_ref, tol, n_sub=9, eps=1.0):
+def fast_tie_fix(grid, x, phi_gpu, phi_ref, tol, n_sub=9, eps=1.0, basis=4):
     """Markers whose GPU sub-cell differs from the oracle's at a sub-cell face.
 
     Returns (n_resolved, n_unresolved): a marker above tolerance counts as
@@ -102,7 +103,7 @@ def fast_tie_fix(grid, x, phi_gpu, phi_ref, tol, n_sub=9, eps=1.0):
                 for ds in (-1, 1):
                     s = s0.copy()
                     s[d] = min(max(s[d] + ds, 0), n_sub - 2)
-                    alt = oracle.shape_fast(grid, xm, eps, n_sub, subcell=s[:, None]).phi[0]
+                    alt = oracle.shape_fast(grid, xm, eps, n_sub, subcell=s[:, None], basis=basis).phi[0]
                     if np.max(np.abs(phi_gpu[m] - alt)) / scale <= tol:
                         ok = True
         resolved += ok

@@ -49,7 +49,7 @@ def test_host_only_calls(lib):
     o = B.mls_options()
     assert lib.mls_options_default(ctypes.byref(o)) == B.MLS_OK
     assert (o.real, o.field, o.n_sub, list(o.brick_log2), o.refine) == (B.MLS_F32, B.MLS_F32, 9, [3, 3, 3], 1)
-    assert o.eps == 1.0 and o.cond_max == 1e6
+    assert o.eps == 1.0 and o.cond_max == 1e6 and o.basis == 4
     assert lib.mls_options_default(None) == B.MLS_ERR_INVALID_ARG
     assert lib.mls_strerror(B.MLS_ERR_CAPACITY).decode().startswith("more markers")
     # NULL handles are rejected before any CUDA call.
@@ -76,3 +76,9 @@ def test_create_rejects_bad_grids_without_gpu(lib):
     faces[1] = (ctypes.c_double * 5)(0, 1, 2, 3, 4)
     g.faces[1] = ctypes.cast(faces[1], ctypes.POINTER(ctypes.c_double))
     assert lib.mls_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == B.MLS_ERR_INVALID_ARG
+    # Only the linear (m = 4) and quadratic (m = 10) bases exist.
+    lib.mls_options_default(ctypes.byref(o))
+    for m in (0, 3, 7, 11):
+        o.basis = m
+        assert lib.mls_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == B.MLS_ERR_INVALID_ARG
+        assert b"basis" in lib.mls_last_error()
