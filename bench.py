@@ -561,6 +561,31 @@ def run_ours(a, rank, world, local):
                             "step": "mls_refine_markers (ratio 0.8, max level 3) timed alone; build (exact) + "
                                     "interp + spread on the refined markers"}
     Tr.close()
+    # exact build with the quadratic basis (m = 10) on the same markers; an
+    # optional extension, so a failure here is reported and does not end the run
+    try:
+        cq = api.Context(w.faces, w.periodic, real=real, brick_log2=tiles, basis=10)
+        Tq = cq.transfer(M)
+        for _ in range(3):
+            cq.build_transfer(Tq, x, area, "exact")
+        torch.cuda.synchronize()
+        cq.timing(True)
+        for _ in range(5):
+            flush.fill_(1.0)
+            cq.build_transfer(Tq, x, area, "exact")
+        torch.cuda.synchronize()
+        kq = cq.read_timing()
+        cq.timing(False)
+        bq = kq["build_exact"][1] / kq["build_exact"][0]
+        others["exact_quadratic"] = {
+            "build_ms": bq, "markers_per_s": M * world / (bq / 1e3),
+            "linear_build_ms": per_launch.get("build_exact"),
+            "fp64_resolves": cq.status(Tq)["refined_fp64"],
+            "step": "mls_build_transfer (exact, basis m = 10): build kernels alone, events on the stream"}
+        Tq.close()
+        cq.close()
+    except Exception as exc:  # noqa: BLE001 - recorded in the output line
+        others["exact_quadratic"] = {"error": str(exc)}
     if "surrogate" in others:
         step("surrogate")
         others["surrogate"]["fallback_rate"] = ctx.status(T)["surrogate_fallback"] / M
