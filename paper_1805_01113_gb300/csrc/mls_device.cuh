@@ -452,7 +452,8 @@ __device__ __forceinline__ void quad_solve(const R L[kQuadPacked], const R b[kQu
 
 // Exact-MLS solve with the quadratic basis: as exact_solve, A y = e_0 with
 // `refine` residual corrections (A re-formed from the moments), cond_1(A)
-// from the column sums of A and of A^-1 (columns of A^-1 by ten solves).
+// from the column sums of A and of A^-1 = M^T M, M = L^-1 (lower triangular,
+// row by row from L M = I), as for the linear basis.
 template <typename R>
 __device__ __forceinline__ bool exact_solve_quad(const AxisNodes<R> s[3], R inv_eps2, int refine, R w[3][3],
                                                  R y[kQuad], R* cond) {
@@ -498,21 +499,42 @@ __device__ __forceinline__ bool exact_solve_quad(const AxisNodes<R> s[3], R inv_
     for (int i = 0; i < kQuad; ++i) y[i] += dy[i];
   }
   if (cond) {
+    R Mi[kQuadPacked];
+#pragma unroll
+    for (int i = 0; i < kQuad; ++i) {
+      Mi[packed(i, i)] = L[packed(i, i)];
+#pragma unroll
+      for (int j = 0; j < i; ++j) {
+        R v = R(0);
+#pragma unroll
+        for (int k = j; k < i; ++k) v += L[packed(i, k)] * Mi[packed(k, j)];
+        Mi[packed(i, j)] = -v * L[packed(i, i)];
+      }
+    }
+    R col[kQuad], icol[kQuad];
+#pragma unroll
+    for (int i = 0; i < kQuad; ++i) col[i] = icol[i] = R(0);
+#pragma unroll
+    for (int i = 0; i < kQuad; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        const R a = fabs(quad_entry(S, i, j));
+        R b = R(0);
+#pragma unroll
+        for (int k = i; k < kQuad; ++k) b += Mi[packed(k, i)] * Mi[packed(k, j)];
+        b = fabs(b);
+        col[j] += a;
+        icol[j] += b;
+        if (i != j) {
+          col[i] += a;
+          icol[i] += b;
+        }
+      }
     R an = R(0), inv_n = R(0);
 #pragma unroll
-    for (int j = 0; j < kQuad; ++j) {
-      R col = R(0), ej[kQuad], xj[kQuad];
-#pragma unroll
-      for (int i = 0; i < kQuad; ++i) {
-        col += fabs(quad_entry(S, i, j));
-        ej[i] = i == j ? R(1) : R(0);
-      }
-      quad_solve(L, ej, xj);
-      R icol = R(0);
-#pragma unroll
-      for (int i = 0; i < kQuad; ++i) icol += fabs(xj[i]);
-      an = fmax(an, col);
-      inv_n = fmax(inv_n, icol);
+    for (int i = 0; i < kQuad; ++i) {
+      an = fmax(an, col[i]);
+      inv_n = fmax(inv_n, icol[i]);
     }
     *cond = an * inv_n;
   }
