@@ -380,7 +380,9 @@ int mls_surrogate_loss_grad(mls_ctx* ctx, const float* X, const float* T, int32_
  * mls_load: reads and validates the whole file before changing the context;
  * then allocates the table if absent, copies it in (after a device
  * synchronise, so launches still using the old table finish first), and sets
- * the surrogate parameters as mls_surrogate_params(set = 1) does.
+ * the surrogate parameters as mls_surrogate_params(set = 1) does.  An
+ * existing table is overwritten in place: its device address, and so any
+ * CUDA graph captured with it, stays valid.
  * MLS_ERR_INVALID_ARG for a missing or unreadable file, a bad magic, version,
  * checksum or layout, or a key that differs from this context's (another grid
  * or option set); the context is then unchanged.  Both are synchronous. */

@@ -199,16 +199,22 @@ int mls_load(mls_ctx* ctx, const char* path) {
 
   cudaError_t e;
   if (table_data) {
-    if (!ctx->table) {
-      if ((e = cudaMalloc(&ctx->table, table_bytes)) != cudaSuccess) {
-        ctx->table = nullptr;
-        return cuda_fail(e, "mls_load: table allocation");
-      }
+    const bool fresh = !ctx->table;
+    if (fresh && (e = cudaMalloc(&ctx->table, table_bytes)) != cudaSuccess) {
+      ctx->table = nullptr;
+      return cuda_fail(e, "mls_load: table allocation");
     }
     // A table in use by launches still in flight is replaced only after they end.
     if ((e = cudaDeviceSynchronize()) != cudaSuccess ||
-        (e = cudaMemcpy(ctx->table, table_data, table_bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
+        (e = cudaMemcpy(ctx->table, table_data, table_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      // A table allocated here never holds partial contents: later fast builds
+      // rebuild it instead.
+      if (fresh) {
+        cudaFree(ctx->table);
+        ctx->table = nullptr;
+      }
       return cuda_fail(e, "mls_load: table copy");
+    }
   }
   if (!theta.empty()) {
     int rc = mls_surrogate_params(ctx, theta.data(), MLS_MLP_PARAMS, 1);
