@@ -41,11 +41,13 @@ def test_exact_at_subnodes(grid, n_sub, basis):
 
 
 @pytest.mark.parametrize("grid", [_grid_uniform(), _grid_stretched()], ids=["uniform", "stretched"])
-def test_partition_of_unity(grid):
+@pytest.mark.parametrize("basis", [4, 10])
+def test_partition_of_unity(grid, basis):
+    """Eq. 9 blends rows that each sum to 1 with weights that sum to 1, for either basis."""
     home = (4, 7, 10)
     t = RNG.uniform(-0.5, 0.5, size=(3, 200))
     x = _markers_in_cell(grid, home, t)
-    f = oracle.shape_fast(grid, x, 1.0, 9)
+    f = oracle.shape_fast(grid, x, 1.0, 9, basis=basis)
     assert np.max(np.abs(f.phi.sum(1) - 1.0)) < 1e-13
 
 
@@ -78,13 +80,13 @@ def test_near_corner_weight_dominates():
         assert np.max(np.abs(f - e)) < 20 * delta
 
 
-def _max_rel_diff(grid, n_sub, m=1000, seed=5):
+def _max_rel_diff(grid, n_sub, m=1000, seed=5, basis=4):
     """Fig. 2a metric: max over markers of max_k |phi_f - phi_e| / max_k |phi_e|."""
     g = np.random.default_rng(seed)
     t = g.uniform(-0.5, 0.5, size=(3, m))
     x = _markers_in_cell(grid, (5, 5, 5), t)
-    f = oracle.shape_fast(grid, x, 1.0, n_sub).phi
-    e = oracle.shape_exact(grid, x, 1.0).phi
+    f = oracle.shape_fast(grid, x, 1.0, n_sub, basis=basis).phi
+    e = oracle.shape_exact(grid, x, 1.0, basis=basis).phi
     return np.max(np.max(np.abs(f - e), axis=1) / np.max(np.abs(e), axis=1))
 
 
@@ -99,3 +101,12 @@ def test_error_falls_with_subnodes():
     # The paper's 2-D figure reports < 3% at 9 points per axis for its (unstated)
     # weight; with this Gaussian in 3-D (8 Shepard corners) it is about 6%.
     assert errs[2] < 0.08
+
+
+def test_error_falls_with_subnodes_quadratic_basis():
+    """Section 2: fast-MLS does not depend on m; with the quadratic basis the
+    difference to exact-MLS still falls at first order in the sub-node spacing."""
+    grid = _grid_uniform()
+    errs = [_max_rel_diff(grid, n, m=300, basis=10) for n in (3, 5, 9, 17)]
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[2] < 0.7 * errs[1] and errs[3] < 0.7 * errs[2]
