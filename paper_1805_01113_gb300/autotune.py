@@ -5,23 +5,66 @@ kernel (markers per tile, accumulator size, halo overlap) and the sort (bin
 count).  For a given grid and a device-resident marker set, each candidate
 context runs build + interpolate + spread a few times; the fastest median
 wins.  Results are cached per (grid shape, periodicity, marker count bucket,
-device name, method) for the life of the process.
+device name, compute capability, method, field type) for the life of the
+process and, when the environment variable MLS_AUTOTUNE_CACHE names a JSON
+file, across processes in that file.
 """
 
+import json
+import os
 import statistics
+import tempfile
 
 import torch
 
 from . import api
 
 CANDIDATES = [(3, 3, 3), (4, 3, 3), (4, 4, 3), (4, 4, 2), (5, 3, 3), (3, 3, 2)]
+CACHE_ENV = "MLS_AUTOTUNE_CACHE"
 _CACHE = {}
+
+
+def _device():
+    return torch.cuda.get_device_name(), tuple(torch.cuda.get_device_capability())
 
 
 def _key(faces, periodic, M, method, field):
     n = tuple(len(f) - 1 for f in faces)
     bucket = 1 << max(0, int(M).bit_length() - 1)
-    return (n, tuple(bool(p) for p in periodic), bucket, torch.cuda.get_device_name(), method, field)
+    name, cap = _device()
+    return (n, tuple(bool(p) for p in periodic), bucket, name, cap, method, field)
+
+
+def _disk_key(k):
+    return json.dumps(k)
+
+
+def disk_load(path, k):
+    """(best, times) stored for key k in the JSON cache file, or None."""
+    try:
+        with open(path) as fh:
+            entry = json.load(fh).get(_disk_key(k))
+    except (OSError, ValueError):
+        return None
+    if not entry:
+        return None
+    times = {tuple(int(v) for v in c.split(",")): float(ms) for c, ms in entry["times"].items()}
+    return tuple(entry["best"]), times
+
+
+def disk_store(path, k, best, times):
+    """Add key k to the JSON cache file (read, update, write to a temporary file, rename)."""
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except (OSError, ValueError):
+        data = {}
+    data[_disk_key(k)] = {"best": list(best), "times": {",".join(map(str, c)): ms for c, ms in times.items()}}
+    d = os.path.dirname(os.path.abspath(path))
+    fd, tmp = tempfile.mkstemp(dir=d, prefix=".autotune")
+    with os.fdopen(fd, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def tune(faces, periodic, x, area, u, F, method="exact", real="f32", field=None, reps=5, candidates=CANDIDATES):
@@ -30,6 +73,12 @@ def tune(faces, periodic, x, area, u, F, method="exact", real="f32", field=None,
     k = _key(faces, periodic, x.shape[1], method, field)
     if k in _CACHE:
         return _CACHE[k]
+    path = os.environ.get(CACHE_ENV)
+    if path:
+        hit = disk_load(path, k)
+        if hit is not None:
+            _CACHE[k] = hit
+            return hit
     M = x.shape[1]
     f = torch.zeros_like(u)
     U = torch.empty((3, M), dtype=x.dtype, device=x.device)
@@ -56,4 +105,6 @@ def tune(faces, periodic, x, area, u, F, method="exact", real="f32", field=None,
         ctx.close()
     best = min(times, key=times.get)
     _CACHE[k] = (best, times)
+    if path:
+        disk_store(path, k, best, times)
     return best, times

@@ -1,0 +1,79 @@
+"""The autotuner's on-disk cache (host logic only, no GPU).
+
+A result stored for one (grid, periodicity, marker-count bucket, device,
+compute capability, method, field) key is returned by a later tune() call
+without timing anything; other keys miss; the file survives concurrent
+additions of different keys and a corrupt file reads as empty.
+"""
+
+import json
+
+import numpy as np
+import pytest
+
+from paper_1805_01113_gb300 import autotune
+
+
+@pytest.fixture
+def fake_device(monkeypatch):
+    monkeypatch.setattr(autotune, "_device", lambda: ("GB300-test", (10, 3)))
+    monkeypatch.setattr(autotune, "_CACHE", {})
+
+
+def _faces(n):
+    return [np.linspace(-1.0, 1.0, n + 1)] * 3
+
+
+class _Shape:
+    """Stands in for a (3, M) marker tensor: tune() reads only its shape before a cache hit."""
+
+    def __init__(self, M):
+        self.shape = (3, M)
+
+
+def test_round_trip_and_miss(tmp_path, fake_device):
+    path = str(tmp_path / "tune.json")
+    k = autotune._key(_faces(64), (True, True, True), 5000, "exact", "f32")
+    assert autotune.disk_load(path, k) is None
+    times = {(3, 3, 3): 0.5, (4, 4, 2): 0.4}
+    autotune.disk_store(path, k, (4, 4, 2), times)
+    assert autotune.disk_load(path, k) == ((4, 4, 2), times)
+    other = autotune._key(_faces(64), (True, True, False), 5000, "exact", "f32")
+    assert autotune.disk_load(path, other) is None
+    autotune.disk_store(path, other, (3, 3, 3), {(3, 3, 3): 0.7})
+    assert autotune.disk_load(path, k) == ((4, 4, 2), times)
+    assert len(json.load(open(path))) == 2
+
+
+def test_tune_uses_the_file_without_timing(tmp_path, monkeypatch, fake_device):
+    path = str(tmp_path / "tune.json")
+    faces, periodic, M = _faces(128), (True, True, True), 61440
+    k = autotune._key(faces, periodic, M, "exact", "f32")
+    autotune.disk_store(path, k, (4, 3, 3), {(4, 3, 3): 0.2, (3, 3, 3): 0.3})
+    monkeypatch.setenv(autotune.CACHE_ENV, path)
+
+    def no_context(*a, **kw):
+        raise AssertionError("a cache hit must not create contexts")
+
+    monkeypatch.setattr(autotune.api, "Context", no_context)
+    best, times = autotune.tune(faces, periodic, _Shape(M), None, None, None)
+    assert best == (4, 3, 3) and times[(3, 3, 3)] == 0.3
+    # Same power-of-two bucket of marker counts: still a hit.
+    assert autotune.tune(faces, periodic, _Shape(M + 1000), None, None, None)[0] == (4, 3, 3)
+
+
+def test_key_separates_device_and_capability(monkeypatch):
+    monkeypatch.setattr(autotune, "_device", lambda: ("GB300-test", (10, 3)))
+    a = autotune._key(_faces(32), (True,) * 3, 100, "exact", "f32")
+    monkeypatch.setattr(autotune, "_device", lambda: ("GB300-test", (10, 0)))
+    b = autotune._key(_faces(32), (True,) * 3, 100, "exact", "f32")
+    assert a != b
+
+
+def test_corrupt_file_reads_as_empty(tmp_path, fake_device):
+    path = tmp_path / "tune.json"
+    path.write_text("{not json")
+    k = autotune._key(_faces(16), (True,) * 3, 10, "fast", "bf16")
+    assert autotune.disk_load(str(path), k) is None
+    autotune.disk_store(str(path), k, (3, 3, 3), {(3, 3, 3): 1.0})
+    assert autotune.disk_load(str(path), k)[0] == (3, 3, 3)
