@@ -111,7 +111,7 @@ def test_header_only_checkpoint(api, tmp_path):
     assert e.value.code == B.MLS_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("change", ["eps", "n_sub", "real", "face", "periodic"])
+@pytest.mark.parametrize("change", ["eps", "n_sub", "real", "face", "periodic", "basis"])
 def test_refuses_other_grid_or_options(api, tmp_path, change):
     faces, periodic = _grid()
     a = api.Context(faces, periodic, real="f32")
@@ -127,6 +127,8 @@ def test_refuses_other_grid_or_options(api, tmp_path, change):
         kw["n_sub"] = 7
     elif change == "real":
         kw["real"] = "f64"
+    elif change == "basis":
+        kw["basis"] = 10
     elif change == "face":
         f2[2][10] = np.nextafter(f2[2][10], np.inf)
     else:
