@@ -177,3 +177,32 @@ def test_direct_forcing_conserves_momentum_and_drops():
     lhs = f.reshape(3, -1).sum(1) * h ** 3
     rhs = (F * area * h).sum(1)
     assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.max(np.abs(rhs))
+
+
+def test_quadratic_basis_interpolates_quadratic_fields():
+    """With m = 10 the interpolation U = Phi^T u reproduces every quadratic field
+    exactly (the linear basis does not), and the scaling factor and Eq. 7
+    conservation are unchanged, since they rest only on the partition of unity."""
+    for _, grid in _grids():
+        x = _markers(grid, 150)
+        q = oracle.shape_exact(grid, x, 1.0, basis=10)
+        lin = oracle.shape_exact(grid, x, 1.0, basis=4)
+        C = RNG.normal(size=(3, 10))
+        mono = lambda X, Y, Z: [np.ones_like(X), X, Y, Z, X * X, Y * Y, Z * Z, X * Y, Y * Z, Z * X]
+        field = np.stack([_field(grid, lambda X, Y, Z, c=c: sum(C[c, i] * t for i, t in enumerate(mono(X, Y, Z))))
+                          for c in range(3)])
+        ref = np.stack([sum(C[c, i] * t for i, t in enumerate(mono(x[0], x[1], x[2]))) for c in range(3)])
+        assert np.max(np.abs(oracle.interpolate(q, field) - ref)) < 1e-11 * np.max(np.abs(ref))
+        assert np.max(np.abs(oracle.interpolate(lin, field) - ref)) > 1e-4 * np.max(np.abs(ref))
+    n = 10
+    grid = oracle.Grid([uniform_faces(n)] * 3, (True, True, True))
+    h = 2.0 / n
+    m = 200
+    x = _markers(grid, m, interior=0)
+    area = RNG.uniform(0.2, 1.0, size=m) * h * h
+    tr = oracle.shape_exact(grid, x, 1.0, basis=10)
+    c = oracle.forcing_scale(tr, area)
+    assert np.max(np.abs(c - area / h ** 2)) < 1e-12
+    F = RNG.normal(size=(3, m))
+    f = oracle.spread(tr, c, F, grid.n).to_dense(grid.n)
+    assert np.max(np.abs(f.reshape(3, -1).sum(1) * h ** 3 - (F * area * h).sum(1))) < 1e-12
