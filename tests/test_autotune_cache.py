@@ -77,3 +77,61 @@ def test_corrupt_file_reads_as_empty(tmp_path, fake_device):
     assert autotune.disk_load(str(path), k) is None
     autotune.disk_store(str(path), k, (3, 3, 3), {(3, 3, 3): 1.0})
     assert autotune.disk_load(str(path), k)[0] == (3, 3, 3)
+
+
+def test_uncached_path_times_every_candidate_and_stores(tmp_path, monkeypatch, fake_device):
+    """The timing loop itself, with the library and CUDA events replaced by fakes:
+    every candidate is timed, the fastest median wins and is written to the file."""
+    path = str(tmp_path / "tune.json")
+    monkeypatch.setenv(autotune.CACHE_ENV, path)
+    cost = {(3, 3, 3): 3.0, (4, 3, 3): 2.0, (4, 4, 3): 2.5, (4, 4, 2): 1.5, (5, 3, 3): 4.0, (3, 3, 2): 1.75}
+    made = []
+
+    class FakeTransfer:
+        def close(self):
+            pass
+
+    class FakeContext:
+        def __init__(self, faces, periodic, real, field, brick_log2):
+            self.b = tuple(brick_log2)
+            made.append(self.b)
+
+        def transfer(self, M):
+            return FakeTransfer()
+
+        def build_transfer(self, *a):
+            FakeEvent.clock += cost[self.b]
+
+        def interpolate(self, *a):
+            pass
+
+        def spread(self, *a):
+            pass
+
+        def close(self):
+            pass
+
+    class FakeEvent:
+        clock = 0.0
+
+        def __init__(self, enable_timing=False):
+            self.t = None
+
+        def record(self, stream=None):
+            self.t = FakeEvent.clock
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    monkeypatch.setattr(autotune.api, "Context", FakeContext)
+    monkeypatch.setattr(autotune.torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(autotune.torch.cuda, "synchronize", lambda: None)
+    import torch
+    x = torch.zeros((3, 100))
+    u = torch.zeros((3, 4, 4, 4))
+    best, times = autotune.tune(_faces(64), (True,) * 3, x, None, u, None)
+    assert best == (4, 4, 2)
+    assert sorted(made) == sorted(autotune.CANDIDATES)
+    assert times == cost
+    k = autotune._key(_faces(64), (True,) * 3, 100, "exact", "f32")
+    assert autotune.disk_load(path, k) == ((4, 4, 2), cost)
