@@ -37,19 +37,24 @@ WORKLOAD_TEXT = {
 }
 
 # Algorithmic bytes per marker of each kernel (float32 path; u_cells = distinct
-# touched cells per marker, measured): the bytes each kernel must move at least.
+# touched cells per marker, measured): the bytes the method must move at least,
+# counted as in the hot-path scope table: the marker's position and area, its
+# 27 shape-function values, its home-cell index and c_l, its force or
+# velocity, and the touched field cells.  The tile-order permutation (4 bytes
+# per marker that the build, interpolation and spreading also read) is this
+# implementation's layout, not the method's, and is not counted.
 def algorithmic_bytes(kernel, rs, u_cells, verts_per_marker):
     return {
         "marker_prep": 12 + 3 * rs * verts_per_marker + 4 * rs,
         "locate": 3 * rs + 8,
         "scatter": 12,
-        "build_exact": 4 + 4 * rs + 27 * rs + rs + 4,
-        "build_fast": 4 + 4 * rs + 27 * rs + rs + 4,
-        "build_surrogate": 4 + 4 * rs + 27 * rs + rs + 4,
-        "interp": 27 * rs + 8 + 3 * rs * u_cells + 3 * rs,
-        "spread": 27 * rs + rs + 8 + 3 * rs + 6 * rs * u_cells,
-        # phi, c, home, perm, V_b in, F and U out, touched u read, touched f read-modify-write
-        "direct_forcing": 27 * rs + rs + 8 + 3 * rs + 3 * rs + 3 * rs + 3 * rs * u_cells + 6 * rs * u_cells,
+        "build_exact": 4 * rs + 27 * rs + rs + 4,
+        "build_fast": 4 * rs + 27 * rs + rs + 4,
+        "build_surrogate": 4 * rs + 27 * rs + rs + 4,
+        "interp": 27 * rs + 4 + 3 * rs * u_cells + 3 * rs,
+        "spread": 27 * rs + rs + 4 + 3 * rs + 6 * rs * u_cells,
+        # phi, c, home, V_b in, F and U out, touched u read, touched f read-modify-write
+        "direct_forcing": 27 * rs + rs + 4 + 3 * rs + 3 * rs + 3 * rs + 3 * rs * u_cells + 6 * rs * u_cells,
     }.get(kernel)
 
 
@@ -59,7 +64,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    p.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"])
     p.add_argument("--method", default="exact", choices=["exact", "fast"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -165,7 +170,7 @@ def run_oracle_sample(name, method, bodies, reps, out, kw=None, fast_too=False, 
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def run_oracle_all_cores(name, method, bodies_each, kw=None):
+def run_oracle_all_cores(name, method, bodies_each, kw=None, return_sample=False):
     """The same oracle, unchanged, in one process per host core at once, each on
     its own bodies_each-body sample of the workload (distinct ranges, wrapping
     around the workload): aggregate markers over the slowest process's compute
@@ -195,7 +200,10 @@ def run_oracle_all_cores(name, method, bodies_each, kw=None):
                 raise RuntimeError("oracle leg failed: " + err[-2000:])
             results.append(json.loads(out.strip().splitlines()[-1]))
     markers = sum(r["markers"] for r in results)
-    return markers / max(r["times"][0] for r in results), procs
+    slowest = max(r["times"][0] for r in results)
+    if return_sample:
+        return markers / slowest, procs, markers, slowest
+    return markers / slowest, procs
 
 
 def _errs(got, ref):
@@ -765,6 +773,35 @@ def run_ours(a, rank, world, local):
             precision["f32_solve_no_refinement"] = {"phi": _errs(o0["phi"], ref["phi"])}
             precision["f32_solve_one_refinement"] = {"phi": errs["exact"]["phi_vs_exact"],
                                                      "fp64_fallbacks": ctx.status(T)["refined_fp64"]}
+        if "surrogate" in others:
+            # The surrogate's gate (linear-reproduction residual of the raw network
+            # output) at several thresholds: fallback rate and build time on the
+            # whole workload, error against the double-precision oracle on the sample.
+            theta = ctx.surrogate_params()
+            sweep = []
+            for thr in (1e-4, 1e-3, 3e-3, 1e-2, 3e-2, float("inf")):
+                cs = api.Context(w.faces, w.periodic, real=real, brick_log2=tiles,
+                                 residual_max=thr if thr != float("inf") else 1e30)
+                cs.surrogate_params(theta)
+                Tsw = cs.transfer(M)
+                for _ in range(2):
+                    cs.build_transfer(Tsw, x, area, "surrogate")
+                torch.cuda.synchronize()
+                cs.read_timing()
+                cs.timing(True)
+                for _ in range(3):
+                    flush.fill_(1.0)
+                    cs.build_transfer(Tsw, x, area, "surrogate")
+                kb = cs.read_timing()["build_surrogate"]
+                cs.timing(False)
+                rate = cs.status(Tsw)["surrogate_fallback"] / M
+                Tsw.close()
+                o = sample_outputs(cs, "surrogate", tdt)
+                sweep.append({"residual_max": thr if thr != float("inf") else None, "fallback_rate": rate,
+                              "build_ms": kb[1] / kb[0], "phi_vs_exact": _errs(o["phi"], ref["phi"]),
+                              "U": _errs(o["U"], ref["U"]), "f": _errs(o["f"], ref["fv"])})
+                cs.close()
+            others["surrogate"]["gate_sweep"] = sweep
 
     line = {
         "metric": METRIC, "value": value, "unit": "markers/s", "n_gpus": world, "steps": a.steps,
@@ -788,26 +825,33 @@ def run_ours(a, rank, world, local):
 # ---------------------------------------------------------------- reference arm
 def run_reference(a, rank, world):
     """The oracle on the host cores: each step runs it, unchanged, in one
-    process per core at once, each process on its own 20-body sample."""
+    process per core at once, each process on its own 20-body sample of the
+    workload.  The line reports what was measured: the sample's markers and the
+    step's time (the slowest process's compute time), not an extrapolation to
+    the whole workload."""
     if rank != 0:
         return
     w = workload(a.workload, a.grid, a.bodies)
     n_bodies = len(w.body_faces) - 1
     nb = min(20, n_bodies)
     kw = {k: v for k, v in (("n", a.grid), ("n_bodies", a.bodies)) if v is not None}
-    rates, procs = [], 1
+    procs, markers, times = 1, 0, []
     steps = max(1, a.steps)
     for s in range(a.warmup + steps):
-        rate, procs = run_oracle_all_cores(a.workload, a.method, nb, kw)
+        _, procs, markers, t = run_oracle_all_cores(a.workload, a.method, nb, kw, return_sample=True)
         if s >= a.warmup:
-            rates.append(rate)
-    value = statistics.mean(rates)
+            times.append(t)
+    step_s = statistics.mean(times)
+    value = markers / step_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "markers/s", "n_gpus": world,
-            "steps": steps, "warmup": a.warmup, "ms_per_step": w.n_markers / value * 1e3,
+            "steps": steps, "warmup": a.warmup, "ms_per_step": 1e3 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[a.workload], "method": a.method,
-                       "sample": f"{procs} processes x {nb} bodies per step, extrapolated per marker"},
+                       "markers_per_step": markers,
+                       "sample": f"each step: {procs} processes at once, each on its own {nb}-body sample of "
+                                 f"the workload ({markers} markers in all); ms_per_step is the slowest "
+                                 "process's compute time"},
             "cpu_baseline": {"value": value, "unit": "markers/s", "cores": procs, "kind": "oracle",
                              "sample": f"{procs} processes at once, each on its own {nb}-body sample of the "
                                        "workload, numpy float64, one thread each"},

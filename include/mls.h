@@ -212,7 +212,7 @@ int mls_spread(mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, void
 int mls_direct_forcing(mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb, double dt,
                        void* U, void* F, void* f, void* stream);
 
-/* Coarse-grained collision detection on the Eulerian mesh (Section 5): a
+/* Coarse-grained collision detection on the Eulerian mesh (Section 4): a
  * cell is a collision cell when markers of more than one body have it as
  * their home cell (the cell of the MLS support built by the last
  * mls_build_transfer on T).
@@ -295,10 +295,14 @@ int mls_fast_table(mls_ctx* ctx, void* stream, const void** table, int64_t* n_cl
  *     count + 1 <= MLS_NOALLOC_MAX_BINS, else MLS_ERR_CAPACITY;
  *   - MLS_FAST needs the context's fast-MLS table to exist already (build it
  *     at set-up with mls_fast_table, which allocates), else MLS_ERR_UNSUPPORTED;
+ *   - MLS_SURROGATE is not offered (its exact-MLS fallback and network
+ *     buffers are not part of the static array): MLS_ERR_UNSUPPORTED;
  *   - no counters are returned: dropped markers are those with home = -1.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array: calls that
+ * before any stream capture.  The address is kept for the life of the
+ * process, which assumes the device's primary context lives as long: after
+ * cudaDeviceReset the kept address is stale and the call must not be used.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other contexts on the same device)
  * race and corrupt each other's results, so serialise them.  The context's
  * device must be current.  Calls no cudaMalloc or cudaFree. */
@@ -385,7 +389,10 @@ int mls_surrogate_loss_grad(mls_ctx* ctx, const float* X, const float* T, int32_
  * CUDA graph captured with it, stays valid.
  * MLS_ERR_INVALID_ARG for a missing or unreadable file, a bad magic, version,
  * checksum or layout, or a key that differs from this context's (another grid
- * or option set); the context is then unchanged.  Both are synchronous. */
+ * or option set), and MLS_ERR_UNSUPPORTED for surrogate parameters in a
+ * context that cannot hold them; the context is then unchanged.  Only a CUDA
+ * failure while copying (MLS_ERR_CUDA) can leave it partly loaded: a new
+ * table without the file's surrogate parameters.  Both are synchronous. */
 int mls_save(mls_ctx* ctx, const char* path);
 int mls_load(mls_ctx* ctx, const char* path);
 

@@ -1,4 +1,4 @@
-"""Coarse-grained collision detection on the Eulerian mesh (Section 5), plain CPU.
+"""Coarse-grained collision detection on the Eulerian mesh (Section 4), plain CPU.
 
 Test infrastructure only: the GPU library never imports this module.
 

@@ -17,10 +17,12 @@ Readings:
     W3[27][64], b3[27];
   * loss: mean squared error over the 27 outputs and the batch; Adam with
     beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
-  * the raw output is projected orthogonally onto the affine set
-    {sum_k phi_k = 1, sum_k phi_k xi_k = 0} (linear reproduction, the
-    property MLS guarantees); a marker whose residual after projection
-    exceeds the threshold (or is not finite) takes the exact-MLS value;
+  * the gate: a marker whose raw network output has a linear-reproduction
+    residual max(|sum_k phi_k - 1|, |sum_k phi_k xi_k,d|) above the threshold
+    (or not finite) takes the exact-MLS value (reproduction of linear fields
+    is the property MLS guarantees, Section 2); an accepted output is then
+    projected orthogonally onto the affine set {sum_k phi_k = 1,
+    sum_k phi_k xi_k = 0};
   * random draws use the splitmix64 finaliser (Steele, Lea & Flood 2014;
     constants as published by Vigna) as a counter-based generator.
 """
@@ -182,9 +184,9 @@ def shape_surrogate(grid, x, theta, eps=1.0, residual_max=1e-4, home=None):
         t[d] = (x[d] - grid.faces[d][sup.home[d]]) / sup.hwidth[d] - 0.5
         xi[d] = (sup.pos[d] - x[d][:, None]) / sup.hwidth[d][:, None]
     Y, _ = forward(theta, features(grid, sup.home, t))
+    res = reproduction_residual(Y, xi)               # the raw output, before projection
     phi, _ = project(Y, xi)
-    res = reproduction_residual(phi, xi)
-    bad = ~(res <= residual_max)
+    bad = ~(res <= residual_max) | ~np.all(np.isfinite(phi), axis=1)
     bad &= sup.ok
     if np.any(bad):
         phi[bad] = _mls.shape_exact(grid, x[:, bad], eps, home=sup.home[:, bad]).phi

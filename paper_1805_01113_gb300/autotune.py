@@ -4,12 +4,14 @@ The transfer step's cost depends on the tile shape through the spreading
 kernel (markers per tile, accumulator size, halo overlap) and the sort (bin
 count).  For a given grid and a device-resident marker set, each candidate
 context runs build + interpolate + spread a few times; the fastest median
-wins.  Results are cached per (grid shape, periodicity, marker count bucket,
-device name, compute capability, method, field type) for the life of the
-process and, when the environment variable MLS_AUTOTUNE_CACHE names a JSON
-file, across processes in that file.
+wins.  Results are cached per (grid shape, a hash of the face coordinates,
+periodicity, marker count bucket, device name, compute capability, method,
+arithmetic type, field type, basis size) for the life of the process and,
+when the environment variable MLS_AUTOTUNE_CACHE names a JSON file, across
+processes in that file.
 """
 
+import hashlib
 import json
 import os
 import statistics
@@ -28,11 +30,22 @@ def _device():
     return torch.cuda.get_device_name(), tuple(torch.cuda.get_device_capability())
 
 
-def _key(faces, periodic, M, method, field):
+def _faces_hash(faces):
+    """16 hex digits of sha256 over the face coordinates (float64, little-endian), axis by axis."""
+    import numpy as np
+    d = hashlib.sha256()
+    for f in faces:
+        d.update(np.ascontiguousarray(np.asarray(f, dtype="<f8")).tobytes())
+        d.update(b"|")
+    return d.hexdigest()[:16]
+
+
+def _key(faces, periodic, M, method, field, real="f32", basis=4):
     n = tuple(len(f) - 1 for f in faces)
     bucket = 1 << max(0, int(M).bit_length() - 1)
     name, cap = _device()
-    return (n, tuple(bool(p) for p in periodic), bucket, name, cap, method, field)
+    return (n, _faces_hash(faces), tuple(bool(p) for p in periodic), bucket, name, cap, method, real, field,
+            int(basis))
 
 
 def _disk_key(k):
@@ -67,10 +80,11 @@ def disk_store(path, k, best, times):
     os.replace(tmp, path)
 
 
-def tune(faces, periodic, x, area, u, F, method="exact", real="f32", field=None, reps=5, candidates=CANDIDATES):
+def tune(faces, periodic, x, area, u, F, method="exact", real="f32", field=None, reps=5, candidates=CANDIDATES,
+         basis=4):
     """Return (best brick_log2, {candidate: median ms}) for build + interp + spread of these markers."""
     field = field or real
-    k = _key(faces, periodic, x.shape[1], method, field)
+    k = _key(faces, periodic, x.shape[1], method, field, real, basis)
     if k in _CACHE:
         return _CACHE[k]
     path = os.environ.get(CACHE_ENV)
@@ -83,10 +97,12 @@ def tune(faces, periodic, x, area, u, F, method="exact", real="f32", field=None,
     f = torch.zeros_like(u)
     U = torch.empty((3, M), dtype=x.dtype, device=x.device)
     times = {}
+    failures = {}
     for b in candidates:
         try:
-            ctx = api.Context(faces, periodic, real=real, field=field, brick_log2=b)
-        except Exception:
+            ctx = api.Context(faces, periodic, real=real, field=field, brick_log2=b, basis=basis)
+        except Exception as exc:  # a shape this grid or device cannot take; the others still compete
+            failures[b] = exc
             continue
         T = ctx.transfer(M)
         ms = []
@@ -103,6 +119,9 @@ def tune(faces, periodic, x, area, u, F, method="exact", real="f32", field=None,
         times[b] = statistics.median(ms)
         T.close()
         ctx.close()
+    if not times:
+        detail = "; ".join(f"{c}: {e}" for c, e in failures.items()) or "no candidates given"
+        raise RuntimeError(f"autotune: no candidate tile shape could be set up ({detail})")
     best = min(times, key=times.get)
     _CACHE[k] = (best, times)
     if path:

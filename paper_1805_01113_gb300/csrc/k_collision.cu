@@ -1,4 +1,4 @@
-// Coarse-grained collision detection on the Eulerian mesh (Section 5): a cell
+// Coarse-grained collision detection on the Eulerian mesh (Section 4): a cell
 // whose markers belong to more than one body is a collision cell, and every
 // marker in it is flagged.  The markers are already grouped by spreading tile,
 // so each tile's cell states live in shared memory for the duration of one

@@ -384,8 +384,9 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_forward_bf16(const unsigned
     for (int o = 0; o < kOut; ++o) Yout[(int64_t)b * kOut + o] = Y[lane * 33 + o];
 }
 
-// Build with the surrogate: features -> network -> projection onto linear
-// reproduction -> residual check (exact-MLS fallback) -> phi, c_l, home.
+// Build with the surrogate: features -> network -> residual check of the raw
+// output (exact-MLS fallback) -> projection onto linear reproduction -> phi,
+// c_l, home.
 struct SurrogateArgs {
   Grid<float> g;
   SurrogateAxes ax;
@@ -476,6 +477,9 @@ __device__ __forceinline__ void surrogate_marker(const SurrogateArgs& a, int64_t
         r[2] += v * s[1].xi[cy];
         r[3] += v * s[2].xi[cz];
       }
+  // The gate: the raw network output's linear-reproduction residual (before
+  // any projection); a marker above residual_max (or not finite) takes exact-MLS.
+  const float rraw = fmaxf(fmaxf(fabsf(r[0]), fabsf(r[1])), fmaxf(fabsf(r[2]), fabsf(r[3])));
   Chol4<float> ch;
   ch.factor(G);
   float lam[4];
@@ -496,9 +500,11 @@ __device__ __forceinline__ void surrogate_marker(const SurrogateArgs& a, int64_t
         res[2] += v * s[1].xi[cy];
         res[3] += v * s[2].xi[cz];
       }
-  const float rmax = fmaxf(fmaxf(fabsf(res[0]), fabsf(res[1])), fmaxf(fabsf(res[2]), fabsf(res[3])));
+  // After the projection the residual is at rounding level; it is checked only
+  // for finiteness (a non-finite projection also takes exact-MLS).
+  const float rproj = fmaxf(fmaxf(fabsf(res[0]), fabsf(res[1])), fmaxf(fabsf(res[2]), fabsf(res[3])));
   ScaleSums<float> sums;
-  if (!(rmax <= a.residual_max)) {
+  if (!(rraw <= a.residual_max) || !isfinite(rproj)) {
     float w[3][3], y[4];
     const bool good = exact_solve<float>(s, a.inv_eps2, 1, w, y, nullptr);
     if (good)

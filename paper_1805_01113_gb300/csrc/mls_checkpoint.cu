@@ -196,6 +196,12 @@ int mls_load(mls_ctx* ctx, const char* path) {
     if (!r.take(theta.data(), theta.size() * sizeof(float))) return bad_file("truncated surrogate parameters");
   }
   if (r.at != r.n) return bad_file("trailing bytes");
+  // The surrogate part needs a context that can hold it: checked before the
+  // table is touched, so a refusal leaves the context as it was.
+  if (!theta.empty()) {
+    int rc = surrogate_check(ctx, "mls_load");
+    if (rc != MLS_OK) return rc;
+  }
 
   cudaError_t e;
   if (table_data) {

@@ -144,7 +144,9 @@ cudaError_t launch_interp_gradient(const mls_ctx* ctx, const mls_transfer* T, co
                                    cudaStream_t s);
 cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, cudaStream_t s);
 cudaError_t launch_spread(const mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, cudaStream_t s);
-// Surrogate (k_mlp.cu).
+// Surrogate (k_mlp.cu, mls_surrogate_api.cu).  surrogate_check: MLS_OK when the
+// context can hold surrogate parameters, else the error (message set).
+int surrogate_check(mls_ctx* ctx, const char* who);
 void mlp_init_params(uint64_t seed, float* theta);
 int surrogate_class_axis(mls_ctx* ctx);
 cudaError_t mlp_configure();
@@ -166,5 +168,6 @@ cudaError_t launch_build_surrogate(const mls_ctx* ctx, mls_transfer* T, const vo
 
 size_t spread_smem_bytes(const mls_ctx* ctx);
 cudaError_t spread_configure(mls_ctx* ctx);
+
 
 }  // namespace mls

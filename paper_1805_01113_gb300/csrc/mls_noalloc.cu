@@ -32,7 +32,9 @@ static_assert(kScratchBytes == MLS_NOALLOC_SCRATCH_BYTES, "header and layout dis
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Host code cannot use g_scratch's name as a device address; its address on
-// each device is looked up once, with that device current, and cached here.
+// each device is looked up once, with that device current, and cached here
+// for the life of the process (the device's primary context is assumed to
+// live as long; after cudaDeviceReset the cached address would be stale).
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
@@ -71,6 +73,10 @@ extern "C" int mls_build_transfer_noalloc(mls_ctx* ctx, const void* x, const voi
     return fail(MLS_ERR_CAPACITY,
                 "mls_build_transfer_noalloc: the grid has more spreading tiles than MLS_NOALLOC_MAX_BINS - 1; "
                 "use a larger brick_log2");
+  if (method == MLS_SURROGATE)
+    return fail(MLS_ERR_UNSUPPORTED,
+                "mls_build_transfer_noalloc: the surrogate is not offered without allocation; use MLS_EXACT or "
+                "MLS_FAST, or mls_build_transfer");
   if (method != MLS_EXACT && method != MLS_FAST)
     return fail(MLS_ERR_INVALID_ARG, "mls_build_transfer_noalloc: unknown method");
   if (M > 0 && (!x || !area || !phi || !c || !home || !perm))

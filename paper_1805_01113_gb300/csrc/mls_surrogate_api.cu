@@ -51,6 +51,10 @@ struct Scratch {
 
 }  // namespace
 
+namespace mls {
+int surrogate_check(mls_ctx* ctx, const char* who) { return need_surrogate_grid(ctx, who); }
+}  // namespace mls
+
 extern "C" {
 
 int mls_train_options_default(mls_train_options* o) {

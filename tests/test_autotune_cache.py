@@ -1,9 +1,11 @@
 """The autotuner's on-disk cache (host logic only, no GPU).
 
-A result stored for one (grid, periodicity, marker-count bucket, device,
-compute capability, method, field) key is returned by a later tune() call
-without timing anything; other keys miss; the file survives concurrent
-additions of different keys and a corrupt file reads as empty.
+A result stored for one (grid shape and faces, periodicity, marker-count
+bucket, device, compute capability, method, arithmetic, field, basis) key is
+returned by a later tune() call without timing anything; other keys miss; the
+file survives concurrent additions of different keys and a corrupt file reads
+as empty; a tuning in which no candidate can be set up fails with a message
+naming the candidates.
 """
 
 import json
@@ -92,7 +94,7 @@ def test_uncached_path_times_every_candidate_and_stores(tmp_path, monkeypatch, f
             pass
 
     class FakeContext:
-        def __init__(self, faces, periodic, real, field, brick_log2):
+        def __init__(self, faces, periodic, real, field, brick_log2, basis=4):
             self.b = tuple(brick_log2)
             made.append(self.b)
 
@@ -135,3 +137,35 @@ def test_uncached_path_times_every_candidate_and_stores(tmp_path, monkeypatch, f
     assert times == cost
     k = autotune._key(_faces(64), (True,) * 3, 100, "exact", "f32")
     assert autotune.disk_load(path, k) == ((4, 4, 2), cost)
+
+
+def test_key_separates_stretched_from_uniform_faces(fake_device):
+    n = 32
+    uniform = _faces(n)
+    xi = np.linspace(0.0, 1.0, n + 1)
+    stretched = [uniform[0], uniform[1], np.tanh(1.5 * (2 * xi - 1)) / np.tanh(1.5)]
+    a = autotune._key(uniform, (True, True, False), 1000, "exact", "f32")
+    b = autotune._key(stretched, (True, True, False), 1000, "exact", "f32")
+    assert a != b
+    assert a == autotune._key([f.copy() for f in uniform], (True, True, False), 1000, "exact", "f32")
+
+
+def test_key_separates_basis_and_arithmetic(fake_device):
+    f = _faces(16)
+    k4 = autotune._key(f, (True,) * 3, 10, "exact", "f32", "f32", 4)
+    k10 = autotune._key(f, (True,) * 3, 10, "exact", "f32", "f32", 10)
+    k64 = autotune._key(f, (True,) * 3, 10, "exact", "f64", "f64", 4)
+    assert len({k4, k10, k64}) == 3
+
+
+def test_no_candidate_gives_a_clear_error(monkeypatch, fake_device):
+    monkeypatch.delenv(autotune.CACHE_ENV, raising=False)
+
+    def refuse(*a, **kw):
+        raise ValueError("tile too large")
+
+    monkeypatch.setattr(autotune.api, "Context", refuse)
+    with pytest.raises(RuntimeError, match=r"no candidate tile shape.*\(3, 3, 3\): tile too large"):
+        import torch
+        autotune.tune(_faces(8), (True,) * 3, torch.zeros((3, 100)), None, torch.zeros((3, 8, 8, 8)), None,
+                      candidates=[(3, 3, 3)])

@@ -25,3 +25,15 @@ def test_all_cores_runs_one_process_per_core():
     assert value > 0
     # a sample larger than the workload is refused rather than truncated
     assert bench.run_oracle_all_cores("c2", "exact", 13, KW) is None
+
+
+def test_reference_arm_reports_the_measured_sample(capsys):
+    class A:
+        workload, grid, bodies, method, steps, warmup = "c2", 64, 12, "exact", 1, 0
+    bench.run_reference(A, 0, 1)
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    procs = max(1, os.cpu_count() or 1)
+    assert line["impl"] == "reference" and line["config"]["markers_per_step"] == procs * 12 * 1280
+    # value is the sample's markers over the measured step time
+    assert abs(line["value"] - line["config"]["markers_per_step"] / (line["ms_per_step"] / 1e3)) <= 1e-6 * line["value"]

@@ -400,3 +400,120 @@ def test_full_size_multibody_sampled(api):
     a2 = float((u.double() * f.double()).sum())
     a_scale = float((U.double().abs() * cF.abs()).sum())
     assert abs(a1 - a2) <= 1e-5 * a_scale
+
+
+def _cells_near(order, keys, n, cell, periodic):
+    """Indices of markers (sorted home keys `keys`, permutation `order`) whose home
+    cell lies within +/-1 of `cell`, wrapping only the periodic axes."""
+    out = []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                c = [cell[0] + dx, cell[1] + dy, cell[2] + dz]
+                ok = True
+                for a in range(3):
+                    if periodic[a]:
+                        c[a] %= n[a]
+                    elif not 0 <= c[a] < n[a]:
+                        ok = False
+                if not ok:
+                    continue
+                k = (c[2] * n[1] + c[1]) * n[0] + c[0]
+                lo, hi = np.searchsorted(keys, k, "left"), np.searchsorted(keys, k, "right")
+                out.append(order[lo:hi])
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
+
+
+def test_full_size_batched_stretched_sampled(api):
+    """10^4 deformed bodies (32 M markers) in 1024^3, tanh-stretched and walled in z:
+    the benchmark's headline workload in its launch configuration (autotuned tiles).
+    Each field has 3 x 2^30 values, so component offsets pass 2^31; sampled
+    markers and cells include the top and bottom z-planes that bodies reach."""
+    from paper_1805_01113_gb300 import autotune
+    w = make_workload("c3")
+    grid = oracle.Grid(w.faces, w.periodic)
+    n = grid.n
+    M = w.n_markers
+    V32 = w.vertices.astype(np.float32)
+    prep = api.Context(w.faces, w.periodic, real="f32")
+    x, area = prep.marker_prep(torch.as_tensor(V32, device=DEV), torch.as_tensor(w.tri, device=DEV))
+    u = field_full_torch(w.modes, w.faces, torch.float32, DEV)
+    F = torch.as_tensor(w.forces().astype(np.float32), device=DEV)
+    tiles, _ = autotune.tune(w.faces, w.periodic, x, area, u, F, "exact", "f32")
+    ctx = api.Context(w.faces, w.periodic, real="f32", brick_log2=tiles)
+    T = ctx.transfer(M)
+    ctx.build_transfer(T, x, area, "exact")
+    U = ctx.interpolate(T, u)
+    f = torch.zeros_like(u)
+    ctx.spread(T, F, f)
+    assert ctx.status(T)["dropped"] == 0
+    phi_g, c_g, home_g = __import__("gpu_helpers").gpu_transfer(ctx, T)
+
+    xall = x.double().cpu().numpy()
+    home3, ok = oracle.locate(grid, xall)
+    assert ok.all()
+    key = (home3[2].astype(np.int64) * n[1] + home3[1]) * n[0] + home3[0]
+    assert np.array_equal(home_g, key)
+    # 2000 sampled markers: random ones plus the lowest and highest in z.
+    rng = np.random.default_rng(1805)
+    zorder = np.argsort(xall[2], kind="stable")
+    s = np.unique(np.concatenate([rng.choice(M, size=1800, replace=False), zorder[:100], zorder[-100:]]))
+    xs, as_ = oracle.marker_prep(V32, w.tri[s], "f32")
+    assert np.array_equal(x[:, s].cpu().numpy(), xs)
+    tr = oracle.shape_exact(grid, xs, 1.0)
+    cs = oracle.forcing_scale(tr, as_)
+    assert normwise(phi_g[s], tr.phi) <= TOL["f32"]
+    assert normwise(c_g[s], cs) <= TOL["f32"]
+    ix, iy, iz = (torch.as_tensor(a, device=DEV) for a in tr.sup.idx)
+    usup = u[:, iz, iy, ix].double().cpu().numpy()
+    U_ref = np.einsum("mk,cmk->cm", tr.phi, usup)
+    assert normwise(U[:, s].double().cpu().numpy(), U_ref) <= TOL["f32"]
+
+    # Spread on sampled touched cells (random ones, plus the top and bottom
+    # touched z-planes), recomputed by the oracle from every marker whose
+    # support covers the cell.
+    order = np.argsort(key, kind="stable")
+    keys = key[order]
+    Fh = F.double().cpu().numpy()
+    areah = area.double().cpu().numpy()
+    touched_z = torch.nonzero(f[0].reshape(n[2], -1).ne(0).any(dim=1)).squeeze(1).cpu().numpy()
+    fflat = f.reshape(3, -1)
+    plane = n[0] * n[1]
+    cand = [rng.choice(torch.nonzero(f[0].reshape(-1) != 0).squeeze(1).cpu().numpy(), size=130, replace=False)]
+    for zp in (touched_z.min(), touched_z.max()):
+        nz_in = torch.nonzero(fflat[0, zp * plane:(zp + 1) * plane] != 0).squeeze(1).cpu().numpy() + zp * plane
+        cand.append(rng.choice(nz_in, size=min(10, len(nz_in)), replace=False))
+    cells = np.concatenate(cand)
+    ref, got = [], []
+    for kc in cells:
+        cell = (int(kc % n[0]), int((kc // n[0]) % n[1]), int(kc // plane))
+        ml = _cells_near(order, keys, n, cell, w.periodic)
+        trm = oracle.shape_exact(grid, xall[:, ml], 1.0)
+        cm = oracle.forcing_scale(trm, areah[ml])
+        lin = (trm.sup.idx[2] * n[1] + trm.sup.idx[1]) * n[0] + trm.sup.idx[0]
+        w_ = np.where(lin == kc, trm.phi, 0.0).sum(1) * cm
+        ref.append((w_[None, :] * Fh[:, ml]).sum(1))
+        got.append(fflat[:, kc].double().cpu().numpy())
+    assert normwise(np.array(got), np.array(ref)) <= TOL["f32"]
+
+    # Conservation (Eq. 7) with the GPU's phi and c: sum_k f_k dV_k equals
+    # sum_l c_l F_l sum_k phi_k^l dV_k (= sum_l F_l dV_l), on a stretched grid.
+    wz = torch.as_tensor(grid.widths[2], device=DEV)
+    hxy = float(grid.widths[0][0] * grid.widths[1][0])
+    lhs = np.array([float((f[q].double().sum(dim=(1, 2)) * wz).sum()) for q in range(3)]) * hxy
+    v = ctx.view(T)
+    hz = (v["home"].long() // plane)
+    dvk = torch.stack([wz[(hz + dz).clamp(0, n[2] - 1)] for dz in (-1, 0, 1)])  # (3, M)
+    ph = v["phi"].double().reshape(3, 9, -1).sum(1)                              # sum over the 9 x,y nodes per z
+    sdv = (ph * dvk).sum(0) * hxy
+    cF = v["c"].double()[None, :] * F.double()[:, v["perm"].long()]
+    rhs = (cF * sdv[None, :]).sum(1).cpu().numpy()
+    scale = (cF.abs() * sdv[None, :].abs()).sum(1).cpu().numpy()
+    assert np.all(np.abs(lhs - rhs) <= 1e-5 * scale)
+    # Adjointness: <U, c F> = <u, f>.
+    cFc = torch.zeros_like(F, dtype=torch.float64)
+    cFc[:, v["perm"].long()] = cF
+    a1 = float((U.double() * cFc).sum())
+    a2 = sum(float((u[q].double() * f[q].double()).sum()) for q in range(3))
+    a_scale = float((U.double().abs() * cFc.abs()).sum())
+    assert abs(a1 - a2) <= 1e-5 * a_scale

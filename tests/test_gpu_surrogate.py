@@ -83,12 +83,16 @@ def test_initialisation_matches_oracle(api):
 
 
 def test_trained_surrogate_builds(api):
-    """Train on a stretched grid; the surrogate's shape functions beat fast-MLS (n = 9) against exact-MLS."""
+    """Train on a stretched grid.  With the gate open (no fallback) the network's
+    projected shape functions beat fast-MLS (n = 9) against exact-MLS; at the
+    default threshold (1e-4 on the raw output's residual) every fallback marker
+    carries exact-MLS, and the fallback rate is reported."""
     w = make_workload("c3", n=96, n_bodies=12)
     grid = oracle.Grid(w.faces, w.periodic)
-    ctx = api.Context(w.faces, w.periodic, real="f32")
+    ctx = api.Context(w.faces, w.periodic, real="f32", residual_max=1e30)
     loss = ctx.train_surrogate(seed=5)                         # default schedule: 131072 Adam steps
     assert loss < 1e-6
+    theta32 = ctx.surrogate_params()
     x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
     sel = np.random.default_rng(3).choice(x.shape[1], size=4000, replace=False)
     xs, as_ = np.ascontiguousarray(x[:, sel]), np.ascontiguousarray(area[sel])
@@ -100,19 +104,78 @@ def test_trained_surrogate_builds(api):
     scale = np.max(np.abs(ex))
     rms_sur = np.sqrt(np.mean((g["phi"] - ex) ** 2)) / scale
     rms_fast = np.sqrt(np.mean((fa - ex) ** 2)) / scale
-    assert g["status"]["dropped"] == 0
-    assert g["status"]["surrogate_fallback"] <= 0.01 * xs.shape[1]
+    assert g["status"]["dropped"] == 0 and g["status"]["surrogate_fallback"] == 0
     # The gain over fast-MLS (the paper's cheap form): smaller error, max and RMS.
     assert err_sur < err_fast and rms_sur < rms_fast
     # Linear reproduction holds by construction (projection).
     assert np.max(np.abs(g["phi"].sum(1) - 1.0)) < 1e-5
     # Same network in double precision (oracle forward + projection): the GPU
     # differs by the bfloat16 evaluation only.
-    theta = ctx.surrogate_params().astype(np.float64)
-    tr, fb = mlp.shape_surrogate(grid, xs, theta)
-    assert normwise(g["phi"], tr.phi) <= BF16_FORWARD_TOL
+    theta = theta32.astype(np.float64)
+    tr, fb = mlp.shape_surrogate(grid, xs, theta, residual_max=1e30)
+    bf16_err = normwise(g["phi"], tr.phi)
+    assert bf16_err <= BF16_FORWARD_TOL
+    # Default gate: the raw residual of the trained network's outputs decides.
+    cd = api.Context(w.faces, w.periodic, real="f32")
+    cd.surrogate_params(theta32)
+    gd = run_gpu(cd, xs, as_, "surrogate")
+    nfb = gd["status"]["surrogate_fallback"]
+    took_exact = np.max(np.abs(gd["phi"] - ex), axis=1) <= 1e-5 * scale
+    assert took_exact.sum() >= nfb                               # every fallback marker is exact-MLS
+    _, fbr = mlp.shape_surrogate(grid, xs, theta)                 # oracle's decision (double precision)
     print(f"surrogate error {err_sur:.3e} (rms {rms_sur:.3e}), fast-MLS error {err_fast:.3e} "
-          f"(rms {rms_fast:.3e}), loss {loss:.3e}, fallback {g['status']['surrogate_fallback']}")
+          f"(rms {rms_fast:.3e}), loss {loss:.3e}, bf16 vs double {bf16_err:.3e}; default gate: fallback "
+          f"{nfb}/{xs.shape[1]} (oracle {int(fbr.sum())})")
+
+
+def _centre_theta(faces):
+    """All weights zero, b3 = exact shape function of a marker at a cell centre:
+    the raw output is that phi for every marker (exact in float32)."""
+    grid = oracle.Grid(faces, (True, True, True))
+    h = [faces[d][1] - faces[d][0] for d in range(3)]
+    centre = np.array([[faces[d][5] + 0.5 * h[d]] for d in range(3)])
+    p = mlp.unflatten(np.zeros(mlp.N_PARAMS))
+    p["b3"] = oracle.shape_exact(grid, centre, 1.0).phi[0].astype(np.float32)
+    return mlp.flatten(p).astype(np.float32)
+
+
+@pytest.mark.parametrize("thr", [0.2, 0.35, 0.45])
+def test_raw_residual_gate_marker_by_marker(api, thr):
+    """The gate reads the raw output's residual.  For the centre network on a
+    uniform grid that residual is max_d |t_d| (t = offset from the cell centre in
+    cell widths), so the fallback set is known in closed form; the GPU must fall
+    back on exactly those markers (up to float32 rounding at the threshold),
+    giving exact-MLS there and the projected centre phi elsewhere."""
+    faces = [uniform_faces(16)] * 3
+    grid = oracle.Grid(faces, (True, True, True))
+    ctx = api.Context(faces, (True, True, True), real="f32", residual_max=thr)
+    theta = _centre_theta(faces)
+    ctx.surrogate_params(theta)
+    rng = np.random.default_rng(int(thr * 100))
+    x = np.stack([rng.uniform(faces[d][2], faces[d][14], size=3000) for d in range(3)]).astype(np.float32)
+    area = np.full(3000, 1e-3, dtype=np.float32)
+    g = run_gpu(ctx, x, area, "surrogate")
+    sup = oracle.support(grid, x.astype(np.float64))
+    t = np.stack([(x[d] - grid.faces[d][sup.home[d]]) / sup.hwidth[d] - 0.5 for d in range(3)])
+    tmax = np.max(np.abs(t), axis=0)
+    want = tmax > thr
+    clear = np.abs(tmax - thr) > 1e-5                           # away from float32 rounding of the residual
+    tr, fb = mlp.shape_surrogate(grid, x.astype(np.float64), theta.astype(np.float64), residual_max=thr)
+    assert np.array_equal(fb[clear], want[clear])                 # the oracle agrees with the closed form
+    ex = oracle.shape_exact(grid, x.astype(np.float64), 1.0).phi
+    xi = np.stack([(sup.pos[d] - x[d][:, None]) / sup.hwidth[d][:, None] for d in range(3)])
+    proj, _ = mlp.project(np.repeat(theta[None, -27:].astype(np.float64), 3000, axis=0), xi)
+    d_ex = np.max(np.abs(g["phi"] - ex), axis=1)
+    d_pr = np.max(np.abs(g["phi"] - proj), axis=1)
+    got = d_ex < d_pr                                            # which of the two the GPU gave
+    distinct = np.max(np.abs(ex - proj), axis=1) > 1e-4
+    m = clear & distinct
+    assert np.array_equal(got[m], want[m])
+    assert np.all(np.minimum(d_ex, d_pr)[m] <= 1e-5)
+    n_clear_fb = int(want[clear].sum())
+    assert abs(g["status"]["surrogate_fallback"] - n_clear_fb) <= int((~clear).sum())
+    assert 0 < want.sum() < len(want)
+
 
 
 def test_surrogate_needs_parameters(api):

@@ -1,4 +1,4 @@
-"""Pins for the coarse collision detection oracle (Section 5).
+"""Pins for the coarse collision detection oracle (Section 4).
 
 The oracle groups markers by home cell (the definition); these tests check it
 against the paper's sequential update rule replayed in a Python loop, against

@@ -113,7 +113,47 @@ def test_surrogate_fallback_paths():
     bad = np.full(mlp.N_PARAMS, np.nan)
     tr, fb = mlp.shape_surrogate(grid, x, bad)
     assert fb.all() and np.max(np.abs(tr.phi - ex)) < 1e-14
-    # Zero network: output 0 projected to the minimum-norm reproducing phi; no fallback.
+    # Zero network: the raw output 0 has residual |sum phi - 1| = 1, so every
+    # marker falls back at the default threshold; above 1 none does, and the
+    # projection gives the minimum-norm reproducing phi.
     tr, fb = mlp.shape_surrogate(grid, x, np.zeros(mlp.N_PARAMS))
+    assert fb.all() and np.max(np.abs(tr.phi - ex)) < 1e-14
+    tr, fb = mlp.shape_surrogate(grid, x, np.zeros(mlp.N_PARAMS), residual_max=1.0 + 1e-9)
     assert not fb.any()
     assert np.max(np.abs(tr.phi.sum(1) - 1)) < 1e-13
+
+
+def centre_network(grid):
+    """Parameters whose output is the exact shape function of a marker at the
+    centre of a uniform cell, whatever the input (all weights zero, b3 = phi)."""
+    h = [grid.faces[d][1] - grid.faces[d][0] for d in range(3)]
+    centre = np.array([[grid.faces[d][5] + 0.5 * h[d]] for d in range(3)])
+    p = mlp.unflatten(np.zeros(mlp.N_PARAMS))
+    p["b3"] = oracle.shape_exact(grid, centre, 1.0).phi[0]
+    return mlp.flatten(p)
+
+
+def test_raw_residual_gate_closed_form():
+    """The gate reads the raw output.  For the centre network on a uniform grid
+    the raw residual is max_d |t_d| (t = offset from the cell centre in cell
+    widths): phi_c sums to 1 and reproduces the centre, so sum_k phi_c,k xi_k,d
+    = -t_d.  Markers fall back exactly where max_d |t_d| > threshold."""
+    grid = oracle.Grid([uniform_faces(16)] * 3, (True, True, True))
+    theta = centre_network(grid)
+    x = _markers(grid, 400)
+    sup = oracle.support(grid, x)
+    t = np.stack([(x[d] - grid.faces[d][sup.home[d]]) / sup.hwidth[d] - 0.5 for d in range(3)])
+    tmax = np.max(np.abs(t), axis=0)
+    ex = oracle.shape_exact(grid, x, 1.0).phi
+    for thr in (0.2, 0.35, 0.45):
+        tr, fb = mlp.shape_surrogate(grid, x, theta, residual_max=thr)
+        assert np.array_equal(fb, tmax > thr)
+        assert np.max(np.abs(tr.phi[fb] - ex[fb])) < 1e-14
+        # accepted markers: the projection of phi_c, which reproduces linear fields at x
+        acc = ~fb
+        xi = np.stack([(sup.pos[d][acc] - x[d][acc, None]) / sup.hwidth[d][acc, None] for d in range(3)])
+        assert np.max(mlp.reproduction_residual(tr.phi[acc], xi)) < 1e-13
+        assert np.max(np.abs(tr.phi[acc] - ex[acc])) < 1.0        # not exact-MLS, only reproducing
+    # Half-way threshold splits the markers in two non-empty sets.
+    _, fb = mlp.shape_surrogate(grid, x, theta, residual_max=0.35)
+    assert 0 < fb.sum() < len(fb)

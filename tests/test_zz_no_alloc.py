@@ -52,7 +52,7 @@ def _noalloc(ctx, x, area, method):
     perm = torch.full((ld,), -7, dtype=torch.int32, device=DEV)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = ctx.lib.mls_build_transfer_noalloc(ctx.handle, C.c_void_p(x.data_ptr()), C.c_void_p(area.data_ptr()), M,
-                                            {"exact": B.MLS_EXACT, "fast": B.MLS_FAST}[method],
+                                            {"exact": B.MLS_EXACT, "fast": B.MLS_FAST, "surrogate": B.MLS_SURROGATE}[method],
                                             C.c_void_p(phi.data_ptr()), C.c_void_p(c.data_ptr()),
                                             C.c_void_p(home.data_ptr()), C.c_void_p(perm.data_ptr()), ld, stream)
     B.check(rc, "mls_build_transfer_noalloc")
@@ -95,6 +95,10 @@ def test_noalloc_build_matches_regular_build():
     ctx.fast_table()
     got, ref = _noalloc(ctx, x, a, "fast"), _regular(ctx, x, a, "fast")
     assert np.array_equal(got[2], ref[2]) and _normwise(got[0], ref[0]) <= TOL
+    # The surrogate is not offered without allocation.
+    with pytest.raises(B.MlsError) as e:
+        _noalloc(ctx, x, a, "surrogate")
+    assert e.value.code == B.MLS_ERR_UNSUPPORTED
     # Sizes beyond the static workspace are refused before any launch.
     big = torch.zeros((3, B.MLS_NOALLOC_MAX_MARKERS + 1), dtype=torch.float32, device=DEV)
     with pytest.raises(B.MlsError) as e:
