@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
           for (int k = 0; k < 27; ++k) {
             const int li = base + (k / 9) * PS + ((k / 3) % 3) * AX + k % 3;
             if (fabsf(p[k]) <= 0.5f) {
-              atomicAdd(&acc[li], round_small(p[k] * q0));
-              atomicAdd(&acc[ACC + li], round_small(p[k] * q1));
-              atomicAdd(&acc[2 * ACC + li], round_small(p[k] * q2));
+              atomicAdd(&acc[li], round_mul(p[k], q0));
+              atomicAdd(&acc[ACC + li], round_mul(p[k], q1));
+              atomicAdd(&acc[2 * ACC + li], round_mul(p[k], q2));
             } else {
               const int gx = wrap(i[0] + k % 3 - 1, D.n[0], D.periodic[0]);
               const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);

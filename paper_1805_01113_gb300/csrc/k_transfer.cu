@@ -1,6 +1,8 @@
 // Euler-to-Lagrange interpolation (gather) and Lagrange-to-Euler spreading
 // (scatter through shared-memory tile accumulators in single precision,
 // direct global reductions in double precision).
+#include <type_traits>
+
 #include "transfer_common.cuh"
 
 namespace mls {
@@ -58,18 +60,24 @@ __global__ void __launch_bounds__(kBlock) k_interp(Dims D, const R* __restrict__
 // flagged rows of the three field components into shared memory with
 // asynchronous copies, then each thread gathers its markers' 27 x 3 values
 // from shared memory.  Blocks then zero U of the dropped markers (the last
-// bin of the tile sort).
+// bin of the tile sort).  A float brick is copied cell by cell; a bfloat16
+// brick keeps the 2-byte values and is copied in 4-byte pairs of cells when
+// the field allows it (`pairs`: an even x extent and a 4-byte aligned field),
+// else cell by cell through registers.
 template <typename FT, int LX>
 __global__ void __launch_bounds__(kInterpThreads) k_interp_brick(
     Dims D, Tiles tl, const float* __restrict__ phi, const int32_t* __restrict__ home,
     const int32_t* __restrict__ perm, const int32_t* __restrict__ items, const int32_t* __restrict__ n_items_p,
     const int32_t* __restrict__ offsets, const int32_t* __restrict__ counts, int64_t M, int64_t cap,
-    const FT* __restrict__ u, float* __restrict__ U) {
+    const FT* __restrict__ u, float* __restrict__ U, int pairs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int BX = (1 << LX) + 2;
-  const InterpSmem L(LX, tl.l[1], tl.l[2]);
+  constexpr bool BF = sizeof(FT) == 2;
+  constexpr int XL = BF ? 2 : 1;                 // halo cells left of the tile in a brick row
+  constexpr int BX = (1 << LX) + 2 * XL;
+  using BT = typename std::conditional<BF, __nv_bfloat16, float>::type;
+  const InterpSmem L(LX, tl.l[1], tl.l[2], BF);
   const int BY = L.BY, PS = L.PS, CELLS = L.CELLS, ROWS = L.ROWS;
-  float* su = reinterpret_cast<float*>(smem_raw);
+  BT* su = reinterpret_cast<BT*>(smem_raw);
   int* row_s = reinterpret_cast<int*>(smem_raw + L.rows);
   int* row_g = row_s + ROWS;
   unsigned char* flag = reinterpret_cast<unsigned char*>(row_g + ROWS);
@@ -98,11 +106,49 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_brick(
       row_g[r] = wrap(oz - 1 + ez, D.n[2], D.periodic[2]) * D.n[1] + wrap(oy - 1 + ey, D.n[1], D.periodic[1]);
     }
     __syncthreads();
-    for (int e = tid; e < ROWS * BX; e += kInterpThreads) {
-      const int r = e / BX, ex = e - r * BX;
-      if (!flag[r]) continue;
-      const int gx = wrap(ox - 1 + ex, D.n[0], D.periodic[0]);
-      stage_cell(su + row_s[r] + ex, CELLS, u, N, (int64_t)row_g[r] * D.n[0] + gx);
+    if constexpr (BF) {
+      if (pairs) {
+        // Pairs of cells [ox - 2 + 2k, ox - 1 + 2k]: even starts, so with an even
+        // x extent a wrapped pair stays a pair and never straddles the last cell.
+        constexpr int BP = BX / 2;
+        for (int e = tid; e < ROWS * BP; e += kInterpThreads) {
+          const int r = e / BP, k = e - r * BP;
+          if (!flag[r]) continue;
+          int gx = ox - XL + 2 * k;
+          if (gx < 0 || gx >= D.n[0]) {
+            if (!D.periodic[0]) continue;             // outside a walled axis: never gathered
+            gx = gx < 0 ? gx + D.n[0] : gx - D.n[0];
+            if (gx < 0 || gx >= D.n[0]) continue;     // beyond one period: never gathered
+          }
+          const int64_t o = (int64_t)row_g[r] * D.n[0] + gx;
+          BT* d = su + row_s[r] + 2 * k;
+          cp_async4_pair(d, u + o);
+          cp_async4_pair(d + CELLS, u + N + o);
+          cp_async4_pair(d + 2 * CELLS, u + 2 * N + o);
+        }
+      } else {
+        for (int e = tid; e < ROWS * BX; e += kInterpThreads) {
+          const int r = e / BX, ex = e - r * BX;
+          if (!flag[r]) continue;
+          int gx = ox - XL + ex;
+          if ((gx < 0 || gx >= D.n[0]) && !D.periodic[0]) continue;
+          gx = wrap(gx, D.n[0], D.periodic[0]);
+          if (gx < 0 || gx >= D.n[0]) continue;
+          const int64_t o = (int64_t)row_g[r] * D.n[0] + gx;
+          BT* d = su + row_s[r] + ex;
+          d[0] = u[o];
+          d[CELLS] = u[N + o];
+          d[2 * CELLS] = u[2 * N + o];
+        }
+      }
+    } else {
+      for (int e = tid; e < ROWS * BX; e += kInterpThreads) {
+        const int r = e / BX, ex = e - r * BX;
+        if (!flag[r]) continue;
+        const int gx = wrap(ox - XL + ex, D.n[0], D.periodic[0]);
+        stage_cell(reinterpret_cast<float*>(su) + row_s[r] + ex, CELLS, reinterpret_cast<const float*>(u), N,
+                   (int64_t)row_g[r] * D.n[0] + gx);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -110,7 +156,7 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_brick(
     for (int j = start + tid; j < end; j += kInterpThreads) {
       int i[3];
       decode_home(home[j], D, i);
-      const int base = (i[2] - oz) * PS + (i[1] - oy) * BX + (i[0] - ox);
+      const int base = (i[2] - oz) * PS + (i[1] - oy) * BX + (i[0] - ox) + (XL - 1);
       float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
       for (int cz = 0; cz < 3; ++cz)
@@ -120,9 +166,9 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_brick(
           for (int cx = 0; cx < 3; ++cx) {
             const float p = phi[(9 * cz + 3 * cy + cx) * cap + j];
             const int si = base + cz * PS + cy * BX + cx;
-            s0 += p * su[si];
-            s1 += p * su[CELLS + si];
-            s2 += p * su[2 * CELLS + si];
+            s0 += p * to_f<BT>(su[si]);
+            s1 += p * to_f<BT>(su[CELLS + si]);
+            s2 += p * to_f<BT>(su[2 * CELLS + si]);
           }
       const int64_t m = perm[j];
       U[m] = s0;
@@ -272,9 +318,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
           for (int k = 0; k < 27; ++k) {
             const int li = base + (k / 9) * PS + ((k / 3) % 3) * AX + k % 3;
             if (fabsf(p[k]) <= 0.5f) {
-              atomicAdd(&acc[li], round_small(p[k] * q0));
-              atomicAdd(&acc[ACC + li], round_small(p[k] * q1));
-              atomicAdd(&acc[2 * ACC + li], round_small(p[k] * q2));
+              atomicAdd(&acc[li], round_mul(p[k], q0));
+              atomicAdd(&acc[ACC + li], round_mul(p[k], q1));
+              atomicAdd(&acc[2 * ACC + li], round_mul(p[k], q2));
             } else {
               const int gx = wrap(i[0] + k % 3 - 1, D.n[0], D.periodic[0]);
               const int gy = wrap(i[1] + (k / 3) % 3 - 1, D.n[1], D.periodic[1]);
@@ -419,7 +465,7 @@ static const void* spread_kernel(int lx, int ly, int lz) {
 
 static cudaError_t interp_configure(mls_ctx* ctx) {
   if (ctx->opt.real == MLS_F64) return cudaSuccess;
-  const int smem = InterpSmem(ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2]).total;
+  const int smem = InterpSmem(ctx->tiles.l[0], ctx->tiles.l[1], ctx->tiles.l[2], ctx->opt.field == MLS_BF16).total;
   const void* k = ctx->opt.field == MLS_F32 ? interp_kernel<float>(ctx->tiles.l[0])
                                             : interp_kernel<__nv_bfloat16>(ctx->tiles.l[0]);
   cudaError_t e;
@@ -460,11 +506,13 @@ cudaError_t launch_interp(const mls_ctx* ctx, const mls_transfer* T, const void*
     Tiles tl = ctx->tiles;
     const float* phi = (const float*)T->phi;
     int64_t M = T->M, cap = T->cap;
+    const bool bf = ctx->opt.field == MLS_BF16;
+    int pairs = bf && D.n[0] % 2 == 0 && (reinterpret_cast<uintptr_t>(u) & 3) == 0 ? 1 : 0;
     void* args[] = {(void*)&D, &tl, (void*)&phi, (void*)&T->home, (void*)&T->perm, (void*)&T->items,
-                    (void*)&T->n_items, (void*)&T->offsets, (void*)&T->counts, &M, &cap, (void*)&u, &U};
-    const void* k = ctx->opt.field == MLS_F32 ? interp_kernel<float>(tl.l[0]) : interp_kernel<__nv_bfloat16>(tl.l[0]);
+                    (void*)&T->n_items, (void*)&T->offsets, (void*)&T->counts, &M, &cap, (void*)&u, &U, &pairs};
+    const void* k = bf ? interp_kernel<__nv_bfloat16>(tl.l[0]) : interp_kernel<float>(tl.l[0]);
     return cudaLaunchKernel(k, dim3(ctx->interp_grid), dim3(kInterpThreads), args,
-                            (size_t)InterpSmem(tl.l[0], tl.l[1], tl.l[2]).total, s);
+                            (size_t)InterpSmem(tl.l[0], tl.l[1], tl.l[2], bf).total, s);
   }
   return cudaGetLastError();
 }

@@ -71,20 +71,28 @@ __device__ __forceinline__ void stage_cell(float* dst, int stride, const __nv_bf
 // one-cell halo, rows of BX = 2^lx + 2 cells, BY rows per plane, BZ planes of
 // stride PS (padded by 4 cells against bank aliasing), three components;
 // then per brick row its offset in the brick, its global row index and a
-// touched flag.
+// touched flag.  A bfloat16 brick keeps the field's 2-byte values and starts
+// each row one cell further left (rows of 2^lx + 4 cells, [ox - 2, ox + 2^lx + 2)),
+// so that it is copied in 4-byte pairs that start on even cells.
 struct InterpSmem {
   int BX, BY, BZ, PS, CELLS, ROWS, rows, total;
-  __host__ __device__ InterpSmem(int lx, int ly, int lz) {
-    BX = (1 << lx) + 2;
+  __host__ __device__ InterpSmem(int lx, int ly, int lz, bool bf16 = false) {
+    BX = (1 << lx) + (bf16 ? 4 : 2);
     BY = (1 << ly) + 2;
     BZ = (1 << lz) + 2;
     PS = BY * BX + 4;
     CELLS = BZ * PS;
     ROWS = BY * BZ;
-    rows = (3 * CELLS * 4 + 15) & ~15;
+    rows = (3 * CELLS * (bf16 ? 2 : 4) + 15) & ~15;
     total = (rows + 8 * ROWS + ROWS + 15) & ~15;
   }
 };
+
+// Asynchronous 4-byte copy of a pair of bfloat16 values.
+__device__ __forceinline__ void cp_async4_pair(__nv_bfloat16* dst, const __nv_bfloat16* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
 
 // Adds four consecutive cells of a field with one vector reduction:
 // 16 bytes of float, or 8 bytes (two bf16x2 pairs) of bfloat16.
@@ -156,9 +164,13 @@ __device__ __forceinline__ void block_max3(float v[3], float* red) {
   }
 }
 
-// round-to-nearest integer of x for |x| <= 2^22: adding 1.5 * 2^23 leaves the
-// integer in the low mantissa bits.
-__device__ __forceinline__ int round_small(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
+// round-to-nearest integer of a * b for |a b| <= 2^22, in one fused
+// multiply-add: a b + 1.5 * 2^23 lies in [2^23, 2^24), where the float spacing
+// is 1, so the single rounding of the fma leaves round(a b) in the low
+// mantissa bits.
+__device__ __forceinline__ int round_mul(float a, float b) {
+  return __float_as_int(__fmaf_rn(a, b, 12582912.0f)) - 0x4B400000;
+}
 
 // Adds one marker's 27 x 3 fixed-point terms round(phi_k q_c) into the shared
 // accumulator, a0 pointing at the stencil's (-1,-1,-1) cell, rows AX cells
@@ -202,9 +214,9 @@ __device__ __forceinline__ void add_stencil_fixed(int* a0, const float p[27], fl
         const int m = 3 * cy + cx;
         const float pk = select3(rc, t[9 * cz + m], t[9 * z1 + m], t[9 * z2 + m]);
         int* a = ar + xo[cx];
-        atomicAdd(a, round_small(pk * q0));
-        atomicAdd(a + ACC, round_small(pk * q1));
-        atomicAdd(a + 2 * ACC, round_small(pk * q2));
+        atomicAdd(a, round_mul(pk, q0));
+        atomicAdd(a + ACC, round_mul(pk, q1));
+        atomicAdd(a + 2 * ACC, round_mul(pk, q2));
       }
     }
   }

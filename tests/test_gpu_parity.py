@@ -274,6 +274,30 @@ def test_bf16_fields(api, brick):
     assert normwise(g["f"], r["f"]) <= 1e-2
 
 
+@pytest.mark.parametrize("layout", ["walled_x", "odd_x"])
+def test_bf16_fields_pair_staging_edges(api, layout):
+    """The bfloat16 interpolation brick is copied in 4-byte pairs of cells when
+    the x extent is even: pairs that would leave a walled x axis are skipped,
+    and an odd x extent falls back to cell-by-cell copies.  Interpolation from
+    identical bfloat16 inputs stays at single-precision accuracy either way."""
+    w = make_workload("c2", n=64, n_bodies=12)
+    if layout == "walled_x":
+        faces, periodic = w.faces, (False, True, True)
+    else:
+        faces, periodic = (uniform_faces(63), w.faces[1], w.faces[2]), w.periodic
+    grid = oracle.Grid(faces, periodic)
+    x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+    u = torch.as_tensor(field_full_np(w.modes, faces), device=DEV).to(torch.bfloat16)
+    F = w.forces().astype(np.float32)
+    for brick in [(3, 3, 3), (2, 3, 2)]:
+        ctx = api.Context(faces, periodic, real="f32", field="bf16", brick_log2=brick)
+        g = run_gpu(ctx, x, area, "exact", u, F)
+        r = run_oracle(grid, x, area, "exact", u.double().cpu().numpy(), F)
+        assert g["status"]["dropped"] == 0
+        assert normwise(g["U"], r["U"]) <= TOL["f32"]
+        assert normwise(g["f"], r["f"]) <= 1e-2
+
+
 def test_rebuild_is_deterministic_per_marker(api):
     w = make_workload("c2", n=64, n_bodies=10)
     x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
