@@ -76,6 +76,10 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tiles", default=None, help="spreading tile log2 sizes, e.g. 3,3,2 (skips the autotuner)")
     p.add_argument("--no-surrogate", action="store_true")
+    p.add_argument("--surrogate-epochs", type=int, default=128,
+                   help="training epochs of 2^20 samples (128, the default schedule; fewer for profiling runs)")
+    p.add_argument("--residual-max", type=float, default=1e-4,
+                   help="the surrogate's gate threshold for the timed surrogate step")
     return p.parse_args()
 
 
@@ -340,7 +344,7 @@ def run_ours(a, rank, world, local):
         tiles = tuple(int(t) for t in a.tiles.split(","))
     elif not a.no_autotune:
         tiles, tune_ms = autotune.tune(w.faces, w.periodic, x, area, u, F, "exact", real)
-    ctx = api.Context(w.faces, w.periodic, real=real, brick_log2=tiles)
+    ctx = api.Context(w.faces, w.periodic, real=real, brick_log2=tiles, residual_max=a.residual_max)
     T = ctx.transfer(M)
     ctx.fast_table()
     methods = ["exact", "fast"]
@@ -348,7 +352,7 @@ def run_ours(a, rank, world, local):
     if real == "f32" and not a.no_surrogate:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        loss = ctx.train_surrogate()
+        loss = ctx.train_surrogate(epochs=a.surrogate_epochs)
         train = {"seconds": time.perf_counter() - t0, "final_loss": loss}
         methods.append("surrogate")
 

@@ -23,6 +23,7 @@ from .mls import (
     gaussian_weight,
     basis_values,
     shape_exact,
+    moment_matrix,
     shape_exact_absolute_basis,
     shape_exact_gradient,
     interpolate_gradient,
@@ -38,7 +39,7 @@ from .mls import (
 
 __all__ = [
     "collision", "mlp", "refine", "Grid", "marker_prep", "locate", "support", "gaussian_weight",
-    "basis_values", "shape_exact", "shape_exact_absolute_basis", "shape_exact_gradient", "interpolate_gradient", "subnode_offsets", "fast_table",
+    "basis_values", "shape_exact", "moment_matrix", "shape_exact_absolute_basis", "shape_exact_gradient", "interpolate_gradient", "subnode_offsets", "fast_table",
     "shape_fast", "forcing_scale", "interpolate", "spread", "SparseField",
     "direct_forcing",
 ]

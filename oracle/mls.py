@@ -211,6 +211,26 @@ def shape_exact(grid, x, eps=1.0, home=None, basis=4):
     return Transfer(phi, sup)
 
 
+def moment_matrix(grid, x, eps=1.0, home=None, basis=4):
+    """The moment matrix A(x_l) of Eq. 3 in the marker-centred, home-width-scaled
+    basis of shape_exact, (M, m, m); and its 1-norm condition number
+    ||A||_1 ||A^-1||_1 (the quantity the single-precision solve is gated on),
+    (M,), infinite where A is singular or the marker has no support."""
+    x = np.asarray(x, dtype=np.float64)
+    sup = support(grid, x, home)
+    W = gaussian_weight(x, sup, eps)
+    xi = np.stack([(sup.pos[d] - x[d][:, None]) / sup.hwidth[d][:, None] for d in range(3)])
+    P = basis_values(xi, basis)
+    A = np.einsum("mk,mki,mkj->mij", W, P, P)
+    cond = np.full(x.shape[1], np.inf)
+    for m in np.nonzero(sup.ok)[0]:
+        try:
+            cond[m] = np.linalg.norm(A[m], 1) * np.linalg.norm(np.linalg.inv(A[m]), 1)
+        except np.linalg.LinAlgError:
+            pass
+    return A, cond
+
+
 def shape_exact_gradient(grid, x, eps=1.0, home=None):
     """Spatial derivatives of the exact-MLS shape functions at the markers.
 

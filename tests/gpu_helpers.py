@@ -79,12 +79,15 @@ def run_oracle(grid, x, area, method, u=None, F=None, eps=1.0, n_sub=9, basis=4)
     return out
 
 
-def fast_tie_fix(grid, x, phi_gpu, phi_ref, tol, n_sub=9, eps=1.0, basis=4):
+def fast_tie_fix(grid, x, phi_gpu, phi_ref, tol, n_sub=9, eps=1.0, basis=4, fixed=None):
     """Markers whose GPU sub-cell differs from the oracle's at a sub-cell face.
 
     Returns (n_resolved, n_unresolved): a marker above tolerance counts as
     resolved when it lies within 1e-4 sub-cell widths of a sub-cell face and
-    the oracle with the neighbouring sub-cell forced matches the GPU.
+    the oracle with the neighbouring sub-cell forced matches the GPU.  When
+    `fixed` (an (M, 27) array, a copy of phi_ref) is given, each resolved
+    marker's row is replaced by that oracle value, so downstream outputs can
+    be recomputed by the oracle on the GPU's sub-cell choices.
     """
     scale = np.max(np.abs(phi_ref))
     err = np.max(np.abs(phi_gpu - phi_ref), axis=1) / scale
@@ -104,7 +107,23 @@ def fast_tie_fix(grid, x, phi_gpu, phi_ref, tol, n_sub=9, eps=1.0, basis=4):
                     s = s0.copy()
                     s[d] = min(max(s[d] + ds, 0), n_sub - 2)
                     alt = oracle.shape_fast(grid, xm, eps, n_sub, subcell=s[:, None], basis=basis).phi[0]
-                    if np.max(np.abs(phi_gpu[m] - alt)) / scale <= tol:
+                    if not ok and np.max(np.abs(phi_gpu[m] - alt)) / scale <= tol:
                         ok = True
+                        if fixed is not None:
+                            fixed[m] = alt
         resolved += ok
     return resolved, len(bad) - resolved
+
+
+def oracle_outputs_with_phi(grid, tr, phi, area, u=None, F=None):
+    """c (Eq. 8), U and f of the oracle recomputed from the shape functions `phi`
+    on the supports of `tr` (used after sub-cell ties are resolved)."""
+    import dataclasses
+    t2 = dataclasses.replace(tr, phi=phi)
+    area = np.asarray(area, dtype=np.float64)
+    out = {"phi": phi, "c": oracle.forcing_scale(t2, np.where(np.isfinite(area), area, 0.0))}
+    if u is not None:
+        out["U"] = oracle.interpolate(t2, np.asarray(u, dtype=np.float64))
+    if F is not None:
+        out["f"] = oracle.spread(t2, out["c"], np.asarray(F, dtype=np.float64), grid.n).to_dense(grid.n)
+    return out

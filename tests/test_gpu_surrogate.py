@@ -17,7 +17,16 @@ from workloads import make_workload, tanh_faces, uniform_faces
 
 pytestmark = pytest.mark.gpu
 
-BF16_FORWARD_TOL = 3e-2      # bfloat16 operands, float32 accumulation, 3 layers
+# bfloat16 keeps 8 significant bits (rounding 2^-9 = 2e-3 relative) on the
+# inputs, the weights and the two hidden activations; each layer sums 64 such
+# products in float32, so its output carries about sqrt(64) x 2e-3 = 1.6e-2 of
+# the typical |w h| terms, and the hidden layers' tanh (hardware approximation,
+# about 2^-11 relative) adds less.  Normwise against the largest output, the
+# measured difference from the double-precision network is 1.8e-2 to 2.1e-2
+# for the trained network's projected phi (test_trained_surrogate_builds
+# prints it) and 4.3e-3 for the initial network's forward pass; the bound
+# leaves a factor of 1.4 over the largest measurement.
+BF16_FORWARD_TOL = 3e-2
 
 
 @pytest.fixture(scope="module")
@@ -71,7 +80,9 @@ def test_forward_f32_and_bf16(api):
     Yr, _ = mlp.forward(theta.astype(np.float64), X.astype(np.float64))
     Xt = torch.as_tensor(X, device=DEV)
     assert normwise(ctx.surrogate_forward(Xt, "f32").double().cpu().numpy(), Yr) <= 1e-5
-    assert normwise(ctx.surrogate_forward(Xt, "bf16").double().cpu().numpy(), Yr) <= BF16_FORWARD_TOL
+    e_bf16 = normwise(ctx.surrogate_forward(Xt, "bf16").double().cpu().numpy(), Yr)
+    print(f"bf16 forward vs double: {e_bf16:.3e}")
+    assert e_bf16 <= BF16_FORWARD_TOL
 
 
 def test_initialisation_matches_oracle(api):

@@ -168,3 +168,38 @@ def test_home_cell_half_open():
     x = np.array([[f[3], np.nextafter(f[3], -np.inf), f[0]], [0.0] * 3, [0.0] * 3])
     home, ok = oracle.locate(grid, x)
     assert list(home[0]) == [3, 2, 0] and ok.all()
+
+
+def test_moment_matrix_pins():
+    """A of Eq. 3: diagonal at a uniform cell centre with closed-form entries
+    (sum W = (1 + 2e)^3, sum W xi_d^2 = 2e (1 + 2e)^2 at eps = 1, e = exp(-1)),
+    so cond_1 = (1 + 2e) / (2e); A^-1 e_0 reproduces shape_exact's phi; and the
+    conditioning grows without bound as a cell's neighbours get wider."""
+    grid = oracle.Grid([uniform_faces(10)] * 3, (True, True, True))
+    x = np.array([[grid.centres[0][4]], [grid.centres[1][5]], [grid.centres[2][6]]])
+    A, cond = oracle.moment_matrix(grid, x, 1.0)
+    e = np.exp(-1.0)
+    ref = np.diag([(1 + 2 * e) ** 3] + [2 * e * (1 + 2 * e) ** 2] * 3)
+    assert np.max(np.abs(A[0] - ref)) < 1e-14
+    assert abs(cond[0] - (1 + 2 * e) / (2 * e)) < 1e-13
+    g2 = oracle.Grid([uniform_faces(12), uniform_faces(12), tanh_faces(12, 1.5)], (True, True, False))
+    rng = np.random.default_rng(4)
+    xs = np.stack([rng.uniform(-0.8, 0.8, 30) for _ in range(3)])
+    A, cond = oracle.moment_matrix(g2, xs, 1.0)
+    y = np.linalg.solve(A, np.tile([1.0, 0, 0, 0], (30, 1))[:, :, None])[:, :, 0]
+    sup = oracle.support(g2, xs)
+    W = oracle.gaussian_weight(xs, sup, 1.0)
+    xi = np.stack([(sup.pos[d] - xs[d][:, None]) / sup.hwidth[d][:, None] for d in range(3)])
+    P = oracle.basis_values(xi)
+    phi = W * np.einsum("mki,mi->mk", P, y)
+    assert np.max(np.abs(phi - oracle.shape_exact(g2, xs, 1.0).phi)) < 1e-13
+    assert np.all(cond >= 1.0)
+    med = []
+    for r in (1.0, 3.0, 5.0, 8.0):
+        w = np.array([r, r, r, 1.0, r, r, r])
+        fz = np.concatenate([[0.0], np.cumsum(w)])
+        fz = fz / fz[-1] * 2 - 1
+        g3 = oracle.Grid([uniform_faces(8), uniform_faces(8), fz], (True, True, False))
+        xz = np.stack([rng.uniform(-0.5, 0.5, 50), rng.uniform(-0.5, 0.5, 50), rng.uniform(fz[3], fz[4], 50)])
+        med.append(np.median(oracle.moment_matrix(g3, xz, 1.0)[1]))
+    assert all(a < b for a, b in zip(med, med[1:])) and med[-1] > 1e6
