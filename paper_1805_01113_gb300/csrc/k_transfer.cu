@@ -257,7 +257,14 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
       const bool act = j < start + cnt;
       int i[3] = {0, 0, 0};
       float v[3] = {0.f, 0.f, 0.f};
+      // The marker's 27 phi values are loaded before the chunk's barrier, so
+      // their latency overlaps the block-wide maximum.
+      float p[27];
+#pragma unroll
+      for (int k = 0; k < 27; ++k) p[k] = 0.f;
       if (act) {
+#pragma unroll
+        for (int k = 0; k < 27; ++k) p[k] = phi[k * cap + j];
         decode_home(home[j], D, i);
         const int64_t m = perm[j];
         const float c = cl[j];
@@ -304,13 +311,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, con
         for (int cz = 0; cz < 3; ++cz)
 #pragma unroll
           for (int cy = 0; cy < 3; ++cy) flag[r0 + cz * AY + cy] = 1;
-        float p[27];
         float pmax = 0.f;
 #pragma unroll
-        for (int k = 0; k < 27; ++k) {
-          p[k] = phi[k * cap + j];
-          pmax = fmaxf(pmax, fabsf(p[k]));
-        }
+        for (int k = 0; k < 27; ++k) pmax = fmaxf(pmax, fabsf(p[k]));
         if (pmax <= 0.5f) {
           add_stencil_fixed(acc + base, p, q0, q1, q2, PS, AX, ACC);
         } else {

@@ -45,6 +45,9 @@ Grid<R> device_grid(const mls_ctx* ctx) {
     a.hi = (R)f.back();
     a.h = (R)(f[1] - f[0]);
     a.inv_h = (R)(1.0 / (f[1] - f[0]));
+    a.bucket = ctx->bucket_d[d];
+    a.nbk = ctx->nbk[d];
+    a.inv_bw = ctx->nbk[d] > 0 ? (R)((double)ctx->nbk[d] / (f.back() - f.front())) : R(0);
   }
   return g;
 }
@@ -155,6 +158,7 @@ static void free_ctx(mls_ctx* c) {
   cudaFree(c->mlp_theta);
   cudaFree(c->mlp_pack);
   cudaFree(c->refine_ws);
+  for (int d = 0; d < 3; ++d) cudaFree(c->bucket_d[d]);
   for (auto& p : c->events) {
     cudaEventDestroy(p.start);
     cudaEventDestroy(p.stop);
@@ -218,6 +222,21 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
     for (int i = 0; i <= n; ++i) ff[i] = (float)grid->faces[d][i];
     for (int i = 0; i < n; ++i) wf[i] = ff[i + 1] - ff[i];
     c->uniform[d] = uni ? 1 : 0;
+    // Bucket table of a non-uniform axis: 4n equal buckets of [faces[0], faces[n]),
+    // each with the cell that contains its lower edge.
+    std::vector<int> bk;
+    if (!uni) {
+      const int nbk = 4 * n;
+      bk.resize(nbk);
+      const double lo = grid->faces[d][0], span = grid->faces[d][n] - lo;
+      int i = 0;
+      for (int b = 0; b < nbk; ++b) {
+        const double edge = lo + span * (double)b / (double)nbk;
+        while (i < n - 1 && grid->faces[d][i + 1] <= edge) ++i;
+        bk[b] = i;
+      }
+      c->nbk[d] = nbk;
+    }
     cudaError_t e;
     if ((e = cudaMalloc(&c->faces_d[d], (n + 1) * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&c->widths_d[d], n * sizeof(double))) != cudaSuccess ||
@@ -228,7 +247,10 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
         (e = cudaMemcpy(c->widths_d[d], w.data(), n * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c->faces_f[d], ff.data(), (n + 1) * sizeof(float), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
-        (e = cudaMemcpy(c->widths_f[d], wf.data(), n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(c->widths_f[d], wf.data(), n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (!bk.empty() && ((e = cudaMalloc(&c->bucket_d[d], bk.size() * sizeof(int))) != cudaSuccess ||
+                         (e = cudaMemcpy(c->bucket_d[d], bk.data(), bk.size() * sizeof(int),
+                                         cudaMemcpyHostToDevice)) != cudaSuccess))) {
       free_ctx(c);
       return cuda_fail(e, "mls_create");
     }

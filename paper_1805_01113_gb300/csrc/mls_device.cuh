@@ -58,6 +58,11 @@ struct Axis {
   int n;
   int periodic;
   int uniform;
+  // Non-uniform axes: [lo, hi) cut into nbk equal buckets; bucket[b] is the
+  // cell containing the bucket's lower edge (device, nbk values).
+  const int* bucket;
+  R inv_bw;         // nbk / (hi - lo) (rounded)
+  int nbk;
 };
 
 template <typename R>
@@ -75,8 +80,10 @@ struct Tiles {
 
 // Home cell of coordinate x on one axis: face_i <= x < face_{i+1}.  Returns -1
 // outside [faces[0], faces[n]) or for NaN.  Uniform axes guess i from
-// (x - lo) * (1/h) and correct it against the face array, so the result agrees
-// with the exact comparison whatever the rounding of the guess.
+// (x - lo) * (1/h), other axes take the cell of x's bucket; the guess is then
+// corrected against the face array, so the result agrees with the exact
+// comparison whatever the rounding of the guess (a bucket holds only a few
+// faces, so the corrections take few steps).
 template <typename R>
 __device__ __forceinline__ int locate_axis(const Axis<R>& a, R x) {
   if (!(x >= a.lo && x < a.hi)) return -1;
@@ -88,12 +95,11 @@ __device__ __forceinline__ int locate_axis(const Axis<R>& a, R x) {
     if (x < a.faces[i]) --i;
     else if (x >= a.faces[i + 1]) ++i;
   } else {
-    int lo = 0, hi = a.n;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (a.faces[mid] <= x) lo = mid; else hi = mid;
-    }
-    i = lo;
+    int b = (int)((x - a.lo) * a.inv_bw);
+    b = b < 0 ? 0 : (b > a.nbk - 1 ? a.nbk - 1 : b);
+    i = __ldg(a.bucket + b);
+    while (i > 0 && x < a.faces[i]) --i;
+    while (i < a.n - 1 && x >= a.faces[i + 1]) ++i;
   }
   return i;
 }

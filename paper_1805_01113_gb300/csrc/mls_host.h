@@ -33,6 +33,8 @@ struct mls_ctx {
   double* widths_d[3];
   float* faces_f[3];
   float* widths_f[3];
+  int* bucket_d[3];      // non-uniform axes: cell of each of nbk equal buckets (device), else nullptr
+  int nbk[3];
   std::vector<double> faces_host[3];
   mls::Tiles tiles;
   // Fast-MLS table, real[n_classes][n_sub^3][27]; class axis -1 when uniform.
