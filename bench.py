@@ -52,6 +52,8 @@ def algorithmic_bytes(kernel, rs, u_cells, verts_per_marker):
         "build_fast": 4 * rs + 27 * rs + rs + 4,
         "build_surrogate": 4 * rs + 27 * rs + rs + 4,
         "interp": 27 * rs + 4 + 3 * rs * u_cells + 3 * rs,
+        # the build's bytes plus the touched u read and U written (phi is not read back)
+        "build_exact_interp": 4 * rs + 27 * rs + rs + 4 + 3 * rs * u_cells + 3 * rs,
         "spread": 27 * rs + rs + 4 + 3 * rs + 6 * rs * u_cells,
         # phi, c, home, V_b in, F and U out, touched u read, touched f read-modify-write
         "direct_forcing": 27 * rs + rs + 4 + 3 * rs + 3 * rs + 3 * rs + 3 * rs * u_cells + 6 * rs * u_cells,
@@ -367,7 +369,12 @@ def run_ours(a, rank, world, local):
             ctx.build_transfer(T, x, area, "exact")
             ctx.direct_forcing(T, u, Vb0, DT, f, F=F_df, U=U)
             return
-        ctx.build_transfer(T, x, area, method)
+        if method == "exact":
+            # the exact step through the build call with the interpolation fused in
+            ctx.build_interpolate(T, x, area, u, U, method="exact")
+            ctx.spread(T, F, f)
+            return
+        ctx.build_transfer(T, x, area, "exact" if method == "exact_separate" else method)
         ctx.interpolate(T, u, U)
         ctx.spread(T, F, f)
 
@@ -490,6 +497,16 @@ def run_ours(a, rank, world, local):
         "kernel_ms": kd, "algorithmic_bytes_per_launch": bd, "achieved_gbs": bd / (kd / 1e3) / 1e9,
         "frac": bd / (kd / 1e3) / 1e9 / pk["hbm_gbs"],
         "separate_interp_spread_ms": per_launch.get("interp", 0.0) + per_launch.get("spread", 0.0)}
+    # the same exact step as three separate calls (build_transfer, interpolate, spread)
+    if a.method == "exact":
+        ms_b, _ = timed("exact_separate", max(3, a.steps // 2), 3, False)
+        _, kt_b = timed("exact_separate", 3, 1, True)
+        kb = {k: n_t[1] / n_t[0] for k, n_t in kt_b.items() if n_t[0]}
+        others["exact_separate"] = {
+            "value": M * world / (statistics.mean(ms_b) / 1e3), "ms_per_step": statistics.mean(ms_b),
+            "step": "marker_prep + build_transfer (exact) + interpolate + spread",
+            "build_ms": kb.get("build_exact"), "interp_ms": kb.get("interp"),
+            "fused_build_interp_ms": per_launch.get("build_exact_interp")}
     # velocity gradient at the markers from the exact-MLS shape-function derivatives
     step(a.method)
     Gt = torch.empty((3, 3, M), dtype=tdt, device=dev)
@@ -625,8 +642,11 @@ def run_ours(a, rank, world, local):
                 F.copy_(F_host, non_blocking=True)
                 ev_f.record(cstream)
             ctx.marker_prep(V, tri, x, area)
-            ctx.build_transfer(T, x, area, a.method)
-            ctx.interpolate(T, u, U)
+            if a.method == "exact":
+                ctx.build_interpolate(T, x, area, u, U, method="exact")
+            else:
+                ctx.build_transfer(T, x, area, a.method)
+                ctx.interpolate(T, u, U)
             ev_u.record(stream)
             with torch.cuda.stream(cstream):
                 cstream.wait_event(ev_u)
@@ -823,7 +843,9 @@ def run_ours(a, rank, world, local):
                    f"{a.workload} variant: {len(w.body_faces) - 1} bodies, {w.n[0]}x{w.n[1]}x{w.n[2]} grid",
                    "markers_per_gpu": M, "method": a.method, "grid": list(w.n),
                    "l2": "flushed by a 256 MiB write before every timed step",
-                   "step": "marker_prep + build_transfer + interpolate + spread",
+                   "step": ("marker_prep + build_interpolate (build and interpolation in one call, the "
+                            "interpolation inside the exact build kernel) + spread" if a.method == "exact" else
+                            "marker_prep + build_transfer + interpolate + spread"),
                    "graph": graph_state["use"], "graph_error": graph_state["error"], "tiles_log2": list(tiles),
                    "autotune_ms": {str(k): round(v, 4) for k, v in tune_ms.items()} if tune_ms else None,
                    "touched_cells_per_marker": round(u_cells, 4)},

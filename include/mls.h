@@ -171,6 +171,20 @@ int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void*
  * Dropped markers get U = 0. */
 int mls_interpolate(mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, void* stream);
 
+/* mls_build_transfer followed by mls_interpolate of the same markers
+ * (Section 2: Eqs. 3-6, then U_l = sum_k phi_k^l u_k, text after Eq. 6), in
+ * one call: the order of an immersed-boundary step, whose markers move before
+ * the velocity is interpolated to them.  For MLS_EXACT with the linear basis
+ * the interpolation is done inside the build kernel, each phi_k multiplied
+ * with the field at its node as it is formed (phi, c, home and perm are still
+ * written to T for a later spread), so the field is read once and phi is not
+ * read back; other methods and bases run the two calls in turn.  Arguments,
+ * outputs and errors are those of the two calls; the results equal theirs up
+ * to the rounding order of the sums (dropped markers get U = 0).
+ *   u  device, field[3][nz][ny][nx]     U  device, real[3][M] (caller's marker order) */
+int mls_build_interpolate(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                          int32_t method, const void* u, void* U, void* stream);
+
 /* Gradients of an interpolated field at the markers (Section 2: MLS also
  * approximates spatial derivatives, which the solver needs for velocity and
  * pressure gradients at the markers): G[c][d][l] = sum_k d_d phi_k^l u_c,k,

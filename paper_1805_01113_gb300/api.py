@@ -139,6 +139,20 @@ class Context:
         T.M = M
         return T
 
+    def build_interpolate(self, T, x, area, u, U=None, method="exact", stream=None):
+        """build_transfer then interpolate in one call (fused into the exact linear-basis build kernel)."""
+        M = x.shape[1]
+        _check_tensor(x, "x", self.real_t, (3, M))
+        _check_tensor(area, "area", self.real_t, (M,))
+        _check_tensor(u, "u", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        if U is None:
+            U = torch.empty((3, M), dtype=self.real_t, device=u.device)
+        _check_tensor(U, "U", self.real_t, (3, M))
+        B.check(self.lib.mls_build_interpolate(self.handle, T.handle, _ptr(x), _ptr(area), M, METHODS[method],
+                                               _ptr(u), _ptr(U), _stream(stream)), "mls_build_interpolate")
+        T.M = M
+        return U
+
     def interpolate(self, T, u, U=None, stream=None):
         _check_tensor(u, "u", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
         if U is None:

@@ -145,6 +145,140 @@ __global__ void __launch_bounds__(kBlock) k_build_exact_redo(BuildArgs<float> a)
   }
 }
 
+// The field and output of an interpolation fused into the exact build:
+// u[3][N] (float, bfloat16 or double storage), U[3][M] in the real type.
+template <typename R, typename FT>
+struct InterpOut {
+  const FT* u;
+  R* U;
+  int64_t N;
+};
+
+template <typename R, typename FT> __device__ __forceinline__ R field_value(const FT* p);
+template <> __device__ __forceinline__ float field_value<float, float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float field_value<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ double field_value<double, double>(const double* p) { return __ldg(p); }
+
+// Global offsets of the 27 support nodes of home cell h: x index per a, row
+// offset (z, y) per (c, b).
+template <typename R>
+__device__ __forceinline__ void support_offsets(const Grid<R>& g, const int h[3], int xs[3], int64_t rows[3][3]) {
+  int ys[3], zs[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    xs[q] = wrap(h[0] + q - 1, g.ax[0].n, g.ax[0].periodic);
+    ys[q] = wrap(h[1] + q - 1, g.ax[1].n, g.ax[1].periodic);
+    zs[q] = wrap(h[2] + q - 1, g.ax[2].n, g.ax[2].periodic);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) rows[c][b] = ((int64_t)zs[c] * g.ax[1].n + ys[b]) * g.ax[0].n;
+}
+
+// Exact-MLS build (Eqs. 3-6, 8) with the interpolation U_l = sum_k phi_k u_k
+// (text after Eq. 6) of the same markers: each phi_k is stored, as in
+// k_build_exact, and multiplied into the three sums with the field at its
+// node as it is formed, so the interpolation reads no phi.  Markers queued for the double re-solve
+// get U from k_build_exact_interp_redo; dropped markers get U = 0.
+// Held to 64 registers (four blocks per SM, as k_build_exact): the field loads
+// of more resident warps overlap (1.97 ms on 32 M markers, against 2.17 ms at
+// 80 registers and 2.07 ms at 48 registers with spills).
+template <typename R, typename FT>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact_interp(BuildArgs<R> a,
+                                                                                      InterpOut<R, FT> io) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.M) return;
+  int h[3];
+  R p[3], ar;
+  AxisNodes<R> s[3];
+  const int64_t m = a.perm[j];
+  if (!marker_setup(a, j, h, p, s, ar)) {
+    io.U[m] = io.U[a.M + m] = io.U[2 * a.M + m] = R(0);
+    return;
+  }
+  R w[3][3], y[4];
+  R cond = R(0);
+  const bool want_cond = sizeof(R) == 4 && a.want_cond;
+  const bool good = exact_solve_m<4>(s, a.inv_eps2, a.refine, w, y, want_cond ? &cond : nullptr);
+  if (sizeof(R) == 4 && (!good || (want_cond && (float)cond > a.cond_max_f))) {
+    a.redo[atomicAdd(&a.status[2], 1ULL)] = (int32_t)j;
+    return;
+  }
+  R U0 = R(0), U1 = R(0), U2 = R(0), c = R(0);
+  if (good) {
+    int xs[3];
+    int64_t rows[3][3];
+    support_offsets(a.g, h, xs, rows);
+    c = exact_scale(s, w, y, ar);
+    exact_emit(s, w, y, [&](int q, int b, int cc, R v) {
+      a.phi[(9 * cc + 3 * b + q) * a.cap + j] = v;
+      const int64_t o = rows[cc][b] + xs[q];
+      U0 += v * field_value<R, FT>(io.u + o);
+      U1 += v * field_value<R, FT>(io.u + io.N + o);
+      U2 += v * field_value<R, FT>(io.u + 2 * io.N + o);
+    });
+  } else {
+#pragma unroll
+    for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = R(0);
+  }
+  a.c[j] = c;
+  a.home[j] = (h[2] * a.g.ax[1].n + h[1]) * a.g.ax[0].n + h[0];
+  io.U[m] = U0;
+  io.U[a.M + m] = U1;
+  io.U[2 * a.M + m] = U2;
+}
+
+// The queued single-precision markers of k_build_exact_interp: solved in
+// double and rounded as in k_build_exact_redo, then interpolated with the
+// rounded phi.
+template <typename FT>
+__global__ void __launch_bounds__(kBlock) k_build_exact_interp_redo(BuildArgs<float> a, InterpOut<float, FT> io) {
+  const unsigned long long n = a.status[2];
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const int64_t j = a.redo[q];
+    const int64_t m = a.perm[j];
+    int h[3];
+    float p[3], ar;
+    AxisNodes<float> s[3];
+    if (!marker_setup(a, j, h, p, s, ar)) {
+      io.U[m] = io.U[a.M + m] = io.U[2 * a.M + m] = 0.f;
+      continue;
+    }
+    AxisNodes<double> sd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sd[d] = axis_nodes(a.gd.ax[d], h[d], (double)p[d]);
+    double wd[3][3], yd[4];
+    const bool good = exact_solve_m<4>(sd, a.inv_eps2_d, 0, wd, yd, (double*)nullptr);
+    ScaleSums<float> sums;
+    float U0 = 0.f, U1 = 0.f, U2 = 0.f;
+    if (good) {
+      int xs[3];
+      int64_t rows[3][3];
+      support_offsets(a.g, h, xs, rows);
+      exact_emit_m<4>(sd, wd, yd, [&](int qq, int b, int c, double v) {
+        const float f = (float)v;
+        a.phi[(9 * c + 3 * b + qq) * a.cap + j] = f;
+        sums.add(s, qq, b, c, f);
+        const int64_t o = rows[c][b] + xs[qq];
+        U0 += f * field_value<float, FT>(io.u + o);
+        U1 += f * field_value<float, FT>(io.u + io.N + o);
+        U2 += f * field_value<float, FT>(io.u + 2 * io.N + o);
+      });
+    } else {
+#pragma unroll
+      for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = 0.f;
+    }
+    marker_finish(a, j, h, s, sums, ar);
+    io.U[m] = U0;
+    io.U[a.M + m] = U1;
+    io.U[2 * a.M + m] = U2;
+  }
+}
+
 // Fast-MLS: the marker's position in its home cell picks the enclosing
 // sub-cell of the n^3 sub-Eulerian mesh; the shape function is the Shepard
 // blend of the 8 corner rows of the table, alpha_i proportional to 1/d_i^2
@@ -334,6 +468,30 @@ cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* 
     launch_build_exact_m<kQuad>(ctx, T, x, area, M, s);
   else
     launch_build_exact_m<4>(ctx, T, x, area, M, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_exact_interp(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area,
+                                      int64_t M, const void* u, void* U, cudaStream_t s) {
+  const int64_t N = (int64_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+  if (ctx->opt.real == MLS_F64) {
+    const InterpOut<double, double> io{(const double*)u, (double*)U, N};
+    k_build_exact_interp<double, double><<<(unsigned)((M + kBlockF64 - 1) / kBlockF64), kBlockF64, 0, s>>>(
+        make_args<double>(ctx, T, x, area, M), io);
+    return cudaGetLastError();
+  }
+  const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  const unsigned redo_grid = (unsigned)std::min<int64_t>(grid, 4 * 152);
+  const BuildArgs<float> a = make_args<float>(ctx, T, x, area, M);
+  if (ctx->opt.field == MLS_BF16) {
+    const InterpOut<float, __nv_bfloat16> io{(const __nv_bfloat16*)u, (float*)U, N};
+    k_build_exact_interp<float, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a, io);
+    k_build_exact_interp_redo<__nv_bfloat16><<<redo_grid, kBlock, 0, s>>>(a, io);
+  } else {
+    const InterpOut<float, float> io{(const float*)u, (float*)U, N};
+    k_build_exact_interp<float, float><<<grid, kBlock, 0, s>>>(a, io);
+    k_build_exact_interp_redo<float><<<redo_grid, kBlock, 0, s>>>(a, io);
+  }
   return cudaGetLastError();
 }
 

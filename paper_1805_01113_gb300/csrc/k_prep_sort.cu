@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R*
                                                    const R* __restrict__ area, int64_t M,
                                                    int32_t* __restrict__ key, int32_t* __restrict__ rank,
                                                    int32_t* __restrict__ counts,
-                                                   unsigned long long* __restrict__ status) {
+                                                   unsigned long long* __restrict__ status,
+                                                   int32_t* __restrict__ sub) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   const R p[3] = {x[j], x[M + j], x[2 * M + j]};
@@ -77,21 +78,34 @@ __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R*
   base = __shfl_sync(peers, base, leader);
   key[j] = k;
   rank[j] = base + __popc(peers & ((1u << lane) - 1u));
+  if (sub && ok)
+    sub[j] = ((((h[2] & ((1 << tl.l[2]) - 1)) << tl.l[1]) | (h[1] & ((1 << tl.l[1]) - 1))) << tl.l[0]) |
+             (h[0] & ((1 << tl.l[0]) - 1));
   if (!ok) {
     atomicAdd(&status[0], 1ULL);
     if (!finite) atomicAdd(&status[1], 1ULL);
   }
 }
 
+// The in-tile sort by home cell runs when a tile has at most kSortCells cells.
+// Until the build overwrites them, three of the transfer's output arrays
+// serve it as scratch: the first plane of phi holds each marker's cell
+// inside its tile (caller order), home the unsorted tile order and c (as
+// int32) the cells in that order.
+bool tile_sort_on(const mls_ctx* ctx) {
+  return ctx->tiles.l[0] + ctx->tiles.l[1] + ctx->tiles.l[2] <= kSortCellsLog2;
+}
+
 cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                           cudaStream_t s) {
   const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  int32_t* sub = tile_sort_on(ctx) ? reinterpret_cast<int32_t*>(T->phi) : nullptr;
   if (ctx->opt.real == MLS_F64)
     k_locate<double><<<grid, kBlock, 0, s>>>(device_grid<double>(ctx), ctx->tiles, (const double*)x,
-                                             (const double*)area, M, T->key, T->rank, T->counts, T->status);
+                                             (const double*)area, M, T->key, T->rank, T->counts, T->status, sub);
   else
     k_locate<float><<<grid, kBlock, 0, s>>>(device_grid<float>(ctx), ctx->tiles, (const float*)x,
-                                            (const float*)area, M, T->key, T->rank, T->counts, T->status);
+                                            (const float*)area, M, T->key, T->rank, T->counts, T->status, sub);
   return cudaGetLastError();
 }
 
@@ -205,19 +219,133 @@ cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx
   return cudaGetLastError();
 }
 
-// perm[offsets[bin] + rank] = caller index: stable within nothing, grouped by bin.
+// perm[offsets[bin] + rank] = caller index: stable within nothing, grouped by
+// bin.  With the in-tile sort, the caller index and the marker's cell in its
+// tile go to the sort's scratch arrays instead (`perm` unsorted, `cell`).
 __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t* __restrict__ key, const int32_t* __restrict__ rank,
                                                     const int32_t* __restrict__ offsets, int64_t M,
-                                                    int32_t* __restrict__ perm) {
+                                                    int32_t* __restrict__ perm, const int32_t* __restrict__ sub,
+                                                    int32_t* __restrict__ cell) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
-  perm[offsets[key[j]] + rank[j]] = (int32_t)j;
+  const int64_t pos = offsets[key[j]] + rank[j];
+  perm[pos] = (int32_t)j;
+  if (cell) cell[pos] = sub[j];
 }
 
-cudaError_t launch_scatter(mls_transfer* T, int64_t M, cudaStream_t s) {
+cudaError_t launch_scatter(const mls_ctx* ctx, mls_transfer* T, int64_t M, cudaStream_t s) {
   const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
-  k_scatter<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->perm);
+  if (tile_sort_on(ctx))
+    k_scatter<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->home,
+                                      reinterpret_cast<const int32_t*>(T->phi), reinterpret_cast<int32_t*>(T->c));
+  else
+    k_scatter<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->perm, nullptr, nullptr);
   return cudaGetLastError();
+}
+
+// Orders the markers of each spreading tile by home cell (counting sort over
+// the tile's cells), so that markers sharing a home cell, and so their 27
+// support nodes, are adjacent in tile order; the order inside one cell is
+// not fixed.  One warp per tile with a private histogram in shared memory
+// (one padding word after every 32 bins, so that the scan's lanes, each
+// owning a run of consecutive bins, read 32 different banks): count,
+// exclusive scan, then each marker takes the next place of its cell.
+// The dropped markers (last bin) keep their places.
+__global__ void __launch_bounds__(kSortThreads) k_tile_sort(Tiles tl, const int32_t* __restrict__ items,
+                                                            const int32_t* __restrict__ n_items_p,
+                                                            const int32_t* __restrict__ offsets,
+                                                            const int32_t* __restrict__ counts, int64_t M,
+                                                            const int32_t* __restrict__ perm0,
+                                                            const int32_t* __restrict__ cell,
+                                                            int32_t* __restrict__ perm) {
+  extern __shared__ int hist_all[];
+  const int C = 1 << (tl.l[0] + tl.l[1] + tl.l[2]);
+  const int lane = threadIdx.x & 31;
+  int* hist = hist_all + (threadIdx.x >> 5) * (C + (C >> 5));
+  const int per = (C + 31) >> 5;          // bins per lane in the scan
+  const int lo = min(C, lane * per), hi = min(C, lo + per);
+  const int n_items = *n_items_p;
+  const int warps = gridDim.x * (kSortThreads / 32);
+  for (int it = blockIdx.x * (kSortThreads / 32) + (threadIdx.x >> 5); it < n_items; it += warps) {
+    const int b = items[it];
+    const int s = offsets[b], n = counts[b];
+    if (n == 1) {
+      if (lane == 0) perm[s] = perm0[s];
+      continue;
+    }
+    for (int q = lane; q < C + (C >> 5); q += 32) hist[q] = 0;
+    __syncwarp();
+    // Windows of 256 markers: the eight loads of a lane are issued together.
+    for (int w0 = 0; w0 < n; w0 += 256) {
+      int cw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = w0 + u * 32 + lane;
+        cw[u] = i < n ? cell[s + i] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (cw[u] >= 0) atomicAdd(&hist[cw[u] + (cw[u] >> 5)], 1);
+    }
+    __syncwarp();
+    int sum = 0;
+    for (int q = lo; q < hi; ++q) sum += hist[q + (q >> 5)];
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int run = incl - sum;
+    for (int q = lo; q < hi; ++q) {
+      const int v = hist[q + (q >> 5)];
+      hist[q + (q >> 5)] = run;
+      run += v;
+    }
+    __syncwarp();
+    for (int w0 = 0; w0 < n; w0 += 256) {
+      int cw[8], pw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = w0 + u * 32 + lane;
+        cw[u] = i < n ? cell[s + i] : -1;
+        pw[u] = i < n ? perm0[s + i] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (cw[u] >= 0) perm[s + atomicAdd(&hist[cw[u] + (cw[u] >> 5)], 1)] = pw[u];
+    }
+    __syncwarp();
+  }
+  const int64_t d0 = offsets[tl.nbins - 1];
+  for (int64_t j = d0 + (int64_t)blockIdx.x * kSortThreads + threadIdx.x; j < M;
+       j += (int64_t)gridDim.x * kSortThreads)
+    perm[j] = perm0[j];
+}
+
+cudaError_t launch_tile_sort(const mls_ctx* ctx, mls_transfer* T, int64_t M, cudaStream_t s) {
+  if (!tile_sort_on(ctx)) return cudaSuccess;
+  const int C = 1 << (ctx->tiles.l[0] + ctx->tiles.l[1] + ctx->tiles.l[2]);
+  const size_t smem = (size_t)(kSortThreads / 32) * (C + (C >> 5)) * 4;
+  k_tile_sort<<<ctx->sort_grid, kSortThreads, smem, s>>>(ctx->tiles, T->items, T->n_items, T->offsets, T->counts, M,
+                                                          T->home, reinterpret_cast<const int32_t*>(T->c), T->perm);
+  return cudaGetLastError();
+}
+
+cudaError_t sort_configure(mls_ctx* ctx) {
+  ctx->sort_grid = 0;
+  if (!tile_sort_on(ctx)) return cudaSuccess;
+  const int C = 1 << (ctx->tiles.l[0] + ctx->tiles.l[1] + ctx->tiles.l[2]);
+  const int smem = (kSortThreads / 32) * (C + (C >> 5)) * 4;
+  cudaError_t e = raise_smem_limit((const void*)k_tile_sort, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_sort, kSortThreads, smem)) != cudaSuccess)
+    return e;
+  ctx->sort_grid = (per_sm > 0 ? per_sm : 1) * sms;
+  return cudaSuccess;
 }
 
 }  // namespace mls

@@ -272,6 +272,7 @@ int mls_create(const mls_grid* grid, const mls_options* opt_in, mls_ctx** out) {
   if (e == cudaSuccess) e = force_configure(c);
   if (e == cudaSuccess) e = collision_configure(c);
   if (e == cudaSuccess) e = build_configure(c);
+  if (e == cudaSuccess) e = sort_configure(c);
   if (e == cudaSuccess) e = mlp_configure();
   if (e != cudaSuccess) {
     free_ctx(c);
@@ -415,8 +416,10 @@ static int ensure_table(mls_ctx* ctx, cudaStream_t s) {
   return MLS_OK;
 }
 
-int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M, int32_t method,
-                       void* stream) {
+// The build of mls_build_transfer; with u (and U) also the interpolation of
+// mls_interpolate, fused into the exact linear-basis build kernel.
+static int build_impl(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M, int32_t method,
+                      void* stream, const void* u, void* U) {
   if (!ctx || !T) return invalid("mls_build_transfer: NULL handle");
   if (T->ctx != ctx) return invalid("mls_build_transfer: transfer belongs to another context");
   if (M < 0) return invalid("mls_build_transfer: negative M");
@@ -454,9 +457,20 @@ int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void*
   e = launch_scan(T, ctx->tiles.nbins, s, ctx);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: scan");
   slot = timer_begin(ctx, "scatter", s);
-  e = launch_scatter(T, M, s);
+  e = launch_scatter(ctx, T, M, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: scatter");
+  slot = timer_begin(ctx, "tile_sort", s);
+  e = launch_tile_sort(ctx, T, M, s);
+  timer_end(ctx, slot, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: tile sort");
+  if (u && method == MLS_EXACT && ctx->opt.basis == 4) {
+    slot = timer_begin(ctx, "build_exact_interp", s);
+    e = launch_build_exact_interp(ctx, T, x, area, M, u, U, s);
+    timer_end(ctx, slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mls_build_interpolate: build");
+    return MLS_OK;
+  }
   slot = timer_begin(ctx, method == MLS_EXACT ? "build_exact" : method == MLS_FAST ? "build_fast" : "build_surrogate",
                      s);
   e = method == MLS_EXACT  ? launch_build_exact(ctx, T, x, area, M, s)
@@ -464,7 +478,25 @@ int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void*
                            : launch_build_surrogate(ctx, T, x, area, M, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: build");
+  if (u) {
+    slot = timer_begin(ctx, "interp", s);
+    e = launch_interp(ctx, T, u, U, s);
+    timer_end(ctx, slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mls_build_interpolate: interpolation");
+  }
   return MLS_OK;
+}
+
+int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M, int32_t method,
+                       void* stream) {
+  return build_impl(ctx, T, x, area, M, method, stream, nullptr, nullptr);
+}
+
+int mls_build_interpolate(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M, int32_t method,
+                          const void* u, void* U, void* stream) {
+  if (M > 0 && (!u || !U)) return invalid("mls_build_interpolate: NULL field or output");
+  if (M == 0) return build_impl(ctx, T, x, area, M, method, stream, nullptr, nullptr);
+  return build_impl(ctx, T, x, area, M, method, stream, u, U);
 }
 
 int mls_interpolate(mls_ctx* ctx, const mls_transfer* T, const void* u, void* U, void* stream) {

@@ -48,6 +48,7 @@ struct mls_ctx {
   int force_grid;        // persistent grid of the fused direct-forcing kernel (0: composed path)
   int collision_grid;    // persistent grid of the collision detection
   int fast_smem_grid;    // persistent grid of the shared-memory fast-MLS build (0: not used)
+  int sort_grid;         // persistent grid of the in-tile sort by home cell (0: tiles too large, no sort)
   void* refine_ws;       // refinement workspace (grown on demand)
   int64_t refine_ws_bytes;
   // Learned surrogate: float32 parameters and the packed bfloat16 copy.
@@ -90,6 +91,8 @@ constexpr int kBlockF64 = 64;         // the same for the double-precision build
 constexpr int kSpreadThreads = 128;   // threads per block of the spreading kernel
 constexpr int kTableRow = 28;         // fast-MLS table row: 27 shape-function values + 1 pad (16-byte rows)
 constexpr int kInterpThreads = 128;   // threads per block of the tile-organised interpolation
+constexpr int kSortThreads = 256;     // threads per block of the in-tile sort (a warp per tile)
+constexpr int kSortCellsLog2 = 12;    // tiles of up to 2^12 cells are sorted by home cell
 
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` (above the
 // 48 KB default).  The limit belongs to the kernel, shared by every context of
@@ -125,11 +128,16 @@ cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri,
 cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                           cudaStream_t s);
 cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx);
-cudaError_t launch_scatter(mls_transfer* T, int64_t M, cudaStream_t s);
+cudaError_t launch_scatter(const mls_ctx* ctx, mls_transfer* T, int64_t M, cudaStream_t s);
+bool tile_sort_on(const mls_ctx* ctx);
+cudaError_t launch_tile_sort(const mls_ctx* ctx, mls_transfer* T, int64_t M, cudaStream_t s);
+cudaError_t sort_configure(mls_ctx* ctx);
 cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                                cudaStream_t s);
 cudaError_t launch_build_fast(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                               cudaStream_t s);
+cudaError_t launch_build_exact_interp(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area,
+                                      int64_t M, const void* u, void* U, cudaStream_t s);
 cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s);
 cudaError_t launch_direct_forcing(const mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb,
                                   double dt, void* U, void* F, void* f, cudaStream_t s);

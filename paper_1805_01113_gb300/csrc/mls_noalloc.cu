@@ -125,8 +125,10 @@ extern "C" int mls_build_transfer_noalloc(mls_ctx* ctx, const void* x, const voi
     return mls::cuda_fail(e, "mls_build_transfer_noalloc: locate");
   if ((e = mls::launch_scan(&T, ctx->tiles.nbins, st, nullptr)) != cudaSuccess)
     return mls::cuda_fail(e, "mls_build_transfer_noalloc: scan");
-  if ((e = mls::launch_scatter(&T, M, st)) != cudaSuccess)
+  if ((e = mls::launch_scatter(ctx, &T, M, st)) != cudaSuccess)
     return mls::cuda_fail(e, "mls_build_transfer_noalloc: scatter");
+  if ((e = mls::launch_tile_sort(ctx, &T, M, st)) != cudaSuccess)
+    return mls::cuda_fail(e, "mls_build_transfer_noalloc: tile sort");
   e = method == MLS_EXACT ? mls::launch_build_exact(ctx, &T, x, area, M, st)
                           : mls::launch_build_fast(ctx, &T, x, area, M, st);
   if (e != cudaSuccess) return mls::cuda_fail(e, "mls_build_transfer_noalloc: build");
