@@ -772,8 +772,7 @@ def run_ours(a, rank, world, local):
 
             def step_b():
                 cb.marker_prep(V, tri, x, area)
-                cb.build_transfer(Tb, x, area, "exact")
-                cb.interpolate(Tb, ub, U)
+                cb.build_interpolate(Tb, x, area, ub, U, method="exact")
                 cb.spread(Tb, F, fb)
 
             for _ in range(3):
