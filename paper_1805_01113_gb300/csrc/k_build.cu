@@ -6,72 +6,13 @@
 #include <cmath>
 #include <limits>
 
-#include "mls_host.h"
+#include "build_common.cuh"
 
 namespace mls {
 
 template <typename R> struct TableVec;
 template <> struct TableVec<float> { using type = float4; };
 template <> struct TableVec<double> { using type = double2; };
-
-template <typename R>
-struct BuildArgs {
-  Grid<R> g;
-  Grid<double> gd;       // double-precision grid for the conditioning fallback
-  const R* x;
-  const R* area;
-  const int32_t* perm;
-  int64_t M, cap;
-  R* phi;
-  R* c;
-  int32_t* home;
-  unsigned long long* status;
-  int32_t* redo;         // markers whose single-precision solve is redone in double (count in status[2])
-  R inv_eps2;
-  double inv_eps2_d;
-  int refine;
-  int want_cond;         // single precision with cond_max > 0
-  float cond_max_f;      // cond_max rounded down to float: cond > cond_max_f <=> cond > cond_max
-  // fast-MLS
-  const R* table;
-  int class_axis;
-  int n_sub;
-};
-
-// Shared prologue: fetch marker perm[j], locate its home cell, and build the
-// per-axis node geometry.  Dropped markers get phi = 0, c = 0, home = -1.
-template <typename R>
-__device__ __forceinline__ bool marker_setup(const BuildArgs<R>& a, int64_t j, int h[3], R p[3],
-                                             AxisNodes<R> s[3], R& ar) {
-  const int64_t m = a.perm[j];
-  p[0] = a.x[m];
-  p[1] = a.x[a.M + m];
-  p[2] = a.x[2 * a.M + m];
-  ar = a.area[m];
-  bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(ar);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    h[d] = locate_axis(a.g.ax[d], p[d]);
-    ok = ok && support_ok(a.g.ax[d], h[d]);
-  }
-  if (!ok) {
-#pragma unroll
-    for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = R(0);
-    a.c[j] = R(0);
-    a.home[j] = -1;
-    return false;
-  }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) s[d] = axis_nodes(a.g.ax[d], h[d], p[d]);
-  return true;
-}
-
-template <typename R>
-__device__ __forceinline__ void marker_finish(const BuildArgs<R>& a, int64_t j, const int h[3],
-                                              const AxisNodes<R> s[3], const ScaleSums<R>& sums, R ar) {
-  a.c[j] = sums.vol != R(0) ? sums.scale(s, ar) : R(0);
-  a.home[j] = (h[2] * a.g.ax[1].n + h[1]) * a.g.ax[0].n + h[0];
-}
 
 // Exact-MLS build (Eqs. 3-6, 8): phi is written node by node as it is formed.
 // A single-precision solve that is ill-conditioned (cond_1(A) > cond_max) or
@@ -145,39 +86,6 @@ __global__ void __launch_bounds__(kBlock) k_build_exact_redo(BuildArgs<float> a)
   }
 }
 
-// The field and output of an interpolation fused into the exact build:
-// u[3][N] (float, bfloat16 or double storage), U[3][M] in the real type.
-template <typename R, typename FT>
-struct InterpOut {
-  const FT* u;
-  R* U;
-  int64_t N;
-};
-
-template <typename R, typename FT> __device__ __forceinline__ R field_value(const FT* p);
-template <> __device__ __forceinline__ float field_value<float, float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float field_value<float, __nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(__ldg(p));
-}
-template <> __device__ __forceinline__ double field_value<double, double>(const double* p) { return __ldg(p); }
-
-// Global offsets of the 27 support nodes of home cell h: x index per a, row
-// offset (z, y) per (c, b).
-template <typename R>
-__device__ __forceinline__ void support_offsets(const Grid<R>& g, const int h[3], int xs[3], int64_t rows[3][3]) {
-  int ys[3], zs[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    xs[q] = wrap(h[0] + q - 1, g.ax[0].n, g.ax[0].periodic);
-    ys[q] = wrap(h[1] + q - 1, g.ax[1].n, g.ax[1].periodic);
-    zs[q] = wrap(h[2] + q - 1, g.ax[2].n, g.ax[2].periodic);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) rows[c][b] = ((int64_t)zs[c] * g.ax[1].n + ys[b]) * g.ax[0].n;
-}
-
 // Exact-MLS build (Eqs. 3-6, 8) with the interpolation U_l = sum_k phi_k u_k
 // (text after Eq. 6) of the same markers: each phi_k is stored, as in
 // k_build_exact, and multiplied into the three sums with the field at its
@@ -210,15 +118,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact_
   R U0 = R(0), U1 = R(0), U2 = R(0), c = R(0);
   if (good) {
     int xs[3];
-    int64_t rows[3][3];
+    int rows[3][3];
     support_offsets(a.g, h, xs, rows);
+    const FT* u0 = io.u;
+    const FT* u1 = u0 + io.N;
+    const FT* u2 = u1 + io.N;
     c = exact_scale(s, w, y, ar);
     exact_emit(s, w, y, [&](int q, int b, int cc, R v) {
       a.phi[(9 * cc + 3 * b + q) * a.cap + j] = v;
-      const int64_t o = rows[cc][b] + xs[q];
-      U0 += v * field_value<R, FT>(io.u + o);
-      U1 += v * field_value<R, FT>(io.u + io.N + o);
-      U2 += v * field_value<R, FT>(io.u + 2 * io.N + o);
+      const int o = rows[cc][b] + xs[q];
+      U0 += v * field_value<R, FT>(u0 + o);
+      U1 += v * field_value<R, FT>(u1 + o);
+      U2 += v * field_value<R, FT>(u2 + o);
     });
   } else {
 #pragma unroll
@@ -257,13 +168,13 @@ __global__ void __launch_bounds__(kBlock) k_build_exact_interp_redo(BuildArgs<fl
     float U0 = 0.f, U1 = 0.f, U2 = 0.f;
     if (good) {
       int xs[3];
-      int64_t rows[3][3];
+      int rows[3][3];
       support_offsets(a.g, h, xs, rows);
       exact_emit_m<4>(sd, wd, yd, [&](int qq, int b, int c, double v) {
         const float f = (float)v;
         a.phi[(9 * c + 3 * b + qq) * a.cap + j] = f;
         sums.add(s, qq, b, c, f);
-        const int64_t o = rows[c][b] + xs[qq];
+        const int o = rows[c][b] + xs[qq];
         U0 += f * field_value<float, FT>(io.u + o);
         U1 += f * field_value<float, FT>(io.u + io.N + o);
         U2 += f * field_value<float, FT>(io.u + 2 * io.N + o);
@@ -417,34 +328,6 @@ __global__ void k_fast_table(Grid<double> gd, int class_axis, int64_t n_classes,
   }
   for (int k = 0; k < 27; ++k) table[idx * kTableRow + k] = (R)phi[k];
   for (int k = 27; k < kTableRow; ++k) table[idx * kTableRow + k] = R(0);
-}
-
-template <typename R>
-static BuildArgs<R> make_args(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M) {
-  BuildArgs<R> a;
-  a.g = device_grid<R>(ctx);
-  a.gd = device_grid<double>(ctx);
-  a.x = (const R*)x;
-  a.area = (const R*)area;
-  a.perm = T->perm;
-  a.M = M;
-  a.cap = T->cap;
-  a.phi = (R*)T->phi;
-  a.c = (R*)T->c;
-  a.home = T->home;
-  a.status = T->status;
-  a.redo = T->key;  // free once the tile sort has scattered
-  a.inv_eps2 = (R)(1.0 / (ctx->opt.eps * ctx->opt.eps));
-  a.inv_eps2_d = 1.0 / (ctx->opt.eps * ctx->opt.eps);
-  a.refine = ctx->opt.real == MLS_F32 ? ctx->opt.refine : 0;
-  a.want_cond = ctx->opt.real == MLS_F32 && ctx->opt.cond_max > 0.0;
-  float t = (float)ctx->opt.cond_max;
-  if ((double)t > ctx->opt.cond_max) t = std::nextafter(t, -std::numeric_limits<float>::infinity());
-  a.cond_max_f = t;
-  a.table = (const R*)ctx->table;
-  a.class_axis = ctx->class_axis;
-  a.n_sub = ctx->opt.n_sub;
-  return a;
 }
 
 template <int MB>
