@@ -369,6 +369,9 @@ def run_ours(a, rank, world, local):
             ctx.build_transfer(T, x, area, "exact")
             ctx.direct_forcing(T, u, Vb0, DT, f, F=F_df, U=U)
             return
+        if method == "build_direct_forcing":
+            ctx.build_direct_forcing(T, x, area, u, Vb0, DT, f, F=F_df, U=U, method="exact")
+            return
         if method == "exact":
             # the exact step through the build call with the interpolation fused in
             ctx.build_interpolate(T, x, area, u, U, method="exact")
@@ -497,6 +500,13 @@ def run_ours(a, rank, world, local):
         "kernel_ms": kd, "algorithmic_bytes_per_launch": bd, "achieved_gbs": bd / (kd / 1e3) / 1e9,
         "frac": bd / (kd / 1e3) / 1e9 / pk["hbm_gbs"],
         "separate_interp_spread_ms": per_launch.get("interp", 0.0) + per_launch.get("spread", 0.0)}
+    # the same immersed-boundary step through one call: the build kernel also interpolates and forms F
+    ms_bd, _ = timed("build_direct_forcing", max(3, a.steps // 2), 3, False)
+    _, kt_bd = timed("build_direct_forcing", 3, 1, True)
+    others["build_direct_forcing"] = {
+        "value": M * world / (statistics.mean(ms_bd) / 1e3), "ms_per_step": statistics.mean(ms_bd),
+        "step": "marker_prep + build_direct_forcing (exact; U and F = (V_b - U)/dt in the build kernel, then spread)",
+        "kernels_ms": {k: round(n_t[1] / n_t[0], 5) for k, n_t in kt_bd.items() if n_t[0]}}
     # the same exact step as three separate calls (build_transfer, interpolate, spread)
     if a.method == "exact":
         ms_b, _ = timed("exact_separate", max(3, a.steps // 2), 3, False)

@@ -226,6 +226,20 @@ int mls_spread(mls_ctx* ctx, const mls_transfer* T, const void* F, void* f, void
 int mls_direct_forcing(mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb, double dt,
                        void* U, void* F, void* f, void* stream);
 
+/* mls_build_transfer followed by mls_direct_forcing of the same markers, in
+ * one call (Section 2: Eqs. 3-6, then the direct-forcing transfer, text after
+ * Eq. 6 and Eq. 7): the immersed-boundary step whose markers have just moved.
+ * For MLS_EXACT with the linear basis the build kernel also interpolates U
+ * and forms F_l = (V_b,l - U_l) / dt as each marker's shape functions are
+ * formed (phi is not read back for the interpolation), and the spread of F
+ * follows; other methods and bases run the two calls in turn.  Arguments,
+ * outputs and errors are those of the two calls (U may be NULL); the results
+ * equal theirs up to the rounding order of the sums.  Dropped markers get
+ * U = 0 and F = 0 and add nothing to f. */
+int mls_build_direct_forcing(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                             int32_t method, const void* u, const void* Vb, double dt, void* U, void* F, void* f,
+                             void* stream);
+
 /* Coarse-grained collision detection on the Eulerian mesh (Section 4): a
  * cell is a collision cell when markers of more than one body have it as
  * their home cell (the cell of the MLS support built by the last

@@ -153,6 +153,26 @@ class Context:
         T.M = M
         return U
 
+    def build_direct_forcing(self, T, x, area, u, Vb, dt, f, F=None, U=None, method="exact", stream=None):
+        """build_transfer then direct_forcing in one call (mls_build_direct_forcing); returns (F, U or None)."""
+        M = x.shape[1]
+        _check_tensor(x, "x", self.real_t, (3, M))
+        _check_tensor(area, "area", self.real_t, (M,))
+        _check_tensor(u, "u", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        _check_tensor(Vb, "Vb", self.real_t, (3, M))
+        _check_tensor(f, "f", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
+        if F is None:
+            F = torch.empty((3, M), dtype=self.real_t, device=u.device)
+        _check_tensor(F, "F", self.real_t, (3, M))
+        if U is not None:
+            _check_tensor(U, "U", self.real_t, (3, M))
+        B.check(self.lib.mls_build_direct_forcing(self.handle, T.handle, _ptr(x), _ptr(area), M, METHODS[method],
+                                                  _ptr(u), _ptr(Vb), float(dt),
+                                                  _ptr(U) if U is not None else None, _ptr(F), _ptr(f),
+                                                  _stream(stream)), "mls_build_direct_forcing")
+        T.M = M
+        return F, U
+
     def interpolate(self, T, u, U=None, stream=None):
         _check_tensor(u, "u", self.field_t, (3, self.n[2], self.n[1], self.n[0]))
         if U is None:

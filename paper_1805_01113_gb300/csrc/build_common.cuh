@@ -75,8 +75,29 @@ __device__ __forceinline__ void marker_finish(const BuildArgs<R>& a, int64_t j, 
 template <typename R, typename FT>
 struct InterpOut {
   const FT* u;
-  R* U;
+  R* U;            // or nullptr: U is formed but not stored
   int64_t N;
+  // Direct forcing (optional, F != nullptr): F_l = (V_b,l - U_l) / dt.
+  const R* Vb;
+  R inv_dt;
+  R* F;
+  // U (and F) of marker m in the caller's order; dropped markers get zeros.
+  __device__ __forceinline__ void store(int64_t m, int64_t M, R U0, R U1, R U2) const {
+    if (U) {
+      U[m] = U0;
+      U[M + m] = U1;
+      U[2 * M + m] = U2;
+    }
+    if (F) {
+      F[m] = (Vb[m] - U0) * inv_dt;
+      F[M + m] = (Vb[M + m] - U1) * inv_dt;
+      F[2 * M + m] = (Vb[2 * M + m] - U2) * inv_dt;
+    }
+  }
+  __device__ __forceinline__ void store_zero(int64_t m, int64_t M) const {
+    if (U) U[m] = U[M + m] = U[2 * M + m] = R(0);
+    if (F) F[m] = F[M + m] = F[2 * M + m] = R(0);
+  }
 };
 
 template <typename R, typename FT> __device__ __forceinline__ R field_value(const FT* p);

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact_
   AxisNodes<R> s[3];
   const int64_t m = a.perm[j];
   if (!marker_setup(a, j, h, p, s, ar)) {
-    io.U[m] = io.U[a.M + m] = io.U[2 * a.M + m] = R(0);
+    io.store_zero(m, a.M);
     return;
   }
   R w[3][3], y[4];
@@ -137,9 +137,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 4 : 1) k_build_exact_
   }
   a.c[j] = c;
   a.home[j] = (h[2] * a.g.ax[1].n + h[1]) * a.g.ax[0].n + h[0];
-  io.U[m] = U0;
-  io.U[a.M + m] = U1;
-  io.U[2 * a.M + m] = U2;
+  io.store(m, a.M, U0, U1, U2);
 }
 
 // The queued single-precision markers of k_build_exact_interp: solved in
@@ -156,7 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_build_exact_interp_redo(BuildArgs<fl
     float p[3], ar;
     AxisNodes<float> s[3];
     if (!marker_setup(a, j, h, p, s, ar)) {
-      io.U[m] = io.U[a.M + m] = io.U[2 * a.M + m] = 0.f;
+      io.store_zero(m, a.M);
       continue;
     }
     AxisNodes<double> sd[3];
@@ -184,9 +182,7 @@ __global__ void __launch_bounds__(kBlock) k_build_exact_interp_redo(BuildArgs<fl
       for (int k = 0; k < 27; ++k) a.phi[k * a.cap + j] = 0.f;
     }
     marker_finish(a, j, h, s, sums, ar);
-    io.U[m] = U0;
-    io.U[a.M + m] = U1;
-    io.U[2 * a.M + m] = U2;
+    io.store(m, a.M, U0, U1, U2);
   }
 }
 
@@ -355,10 +351,12 @@ cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* 
 }
 
 cudaError_t launch_build_exact_interp(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area,
-                                      int64_t M, const void* u, void* U, cudaStream_t s) {
+                                      int64_t M, const void* u, void* U, cudaStream_t s, const void* Vb, double dt,
+                                      void* F) {
   const int64_t N = (int64_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+  const double inv_dt = F ? 1.0 / dt : 0.0;
   if (ctx->opt.real == MLS_F64) {
-    const InterpOut<double, double> io{(const double*)u, (double*)U, N};
+    const InterpOut<double, double> io{(const double*)u, (double*)U, N, (const double*)Vb, inv_dt, (double*)F};
     k_build_exact_interp<double, double><<<(unsigned)((M + kBlockF64 - 1) / kBlockF64), kBlockF64, 0, s>>>(
         make_args<double>(ctx, T, x, area, M), io);
     return cudaGetLastError();
@@ -367,11 +365,12 @@ cudaError_t launch_build_exact_interp(const mls_ctx* ctx, mls_transfer* T, const
   const unsigned redo_grid = (unsigned)std::min<int64_t>(grid, 4 * 152);
   const BuildArgs<float> a = make_args<float>(ctx, T, x, area, M);
   if (ctx->opt.field == MLS_BF16) {
-    const InterpOut<float, __nv_bfloat16> io{(const __nv_bfloat16*)u, (float*)U, N};
+    const InterpOut<float, __nv_bfloat16> io{(const __nv_bfloat16*)u, (float*)U, N, (const float*)Vb, (float)inv_dt,
+                                             (float*)F};
     k_build_exact_interp<float, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a, io);
     k_build_exact_interp_redo<__nv_bfloat16><<<redo_grid, kBlock, 0, s>>>(a, io);
   } else {
-    const InterpOut<float, float> io{(const float*)u, (float*)U, N};
+    const InterpOut<float, float> io{(const float*)u, (float*)U, N, (const float*)Vb, (float)inv_dt, (float*)F};
     k_build_exact_interp<float, float><<<grid, kBlock, 0, s>>>(a, io);
     k_build_exact_interp_redo<float><<<redo_grid, kBlock, 0, s>>>(a, io);
   }

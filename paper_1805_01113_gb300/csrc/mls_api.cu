@@ -419,7 +419,8 @@ static int ensure_table(mls_ctx* ctx, cudaStream_t s) {
 // The build of mls_build_transfer; with u (and U) also the interpolation of
 // mls_interpolate, fused into the exact linear-basis build kernel.
 static int build_impl(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M, int32_t method,
-                      void* stream, const void* u, void* U) {
+                      void* stream, const void* u, void* U, const void* Vb = nullptr, double dt = 0.0,
+                      void* F = nullptr, void* f = nullptr) {
   if (!ctx || !T) return invalid("mls_build_transfer: NULL handle");
   if (T->ctx != ctx) return invalid("mls_build_transfer: transfer belongs to another context");
   if (M < 0) return invalid("mls_build_transfer: negative M");
@@ -465,10 +466,16 @@ static int build_impl(mls_ctx* ctx, mls_transfer* T, const void* x, const void* 
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: tile sort");
   if (u && method == MLS_EXACT && ctx->opt.basis == 4) {
-    slot = timer_begin(ctx, "build_exact_interp", s);
-    e = launch_build_exact_interp(ctx, T, x, area, M, u, U, s);
+    slot = timer_begin(ctx, F ? "build_exact_forcing" : "build_exact_interp", s);
+    e = launch_build_exact_interp(ctx, T, x, area, M, u, U, s, Vb, dt, F);
     timer_end(ctx, slot, s);
     if (e != cudaSuccess) return cuda_fail(e, "mls_build_interpolate: build");
+    if (F) {
+      slot = timer_begin(ctx, "spread", s);
+      e = launch_spread(ctx, T, F, f, s);
+      timer_end(ctx, slot, s);
+      if (e != cudaSuccess) return cuda_fail(e, "mls_build_direct_forcing: spread");
+    }
     return MLS_OK;
   }
   slot = timer_begin(ctx, method == MLS_EXACT ? "build_exact" : method == MLS_FAST ? "build_fast" : "build_surrogate",
@@ -478,7 +485,12 @@ static int build_impl(mls_ctx* ctx, mls_transfer* T, const void* x, const void* 
                            : launch_build_surrogate(ctx, T, x, area, M, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: build");
-  if (u) {
+  if (F) {
+    slot = timer_begin(ctx, "direct_forcing", s);
+    e = launch_direct_forcing(ctx, T, u, Vb, dt, U, F, f, s);
+    timer_end(ctx, slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mls_build_direct_forcing: direct forcing");
+  } else if (u) {
     slot = timer_begin(ctx, "interp", s);
     e = launch_interp(ctx, T, u, U, s);
     timer_end(ctx, slot, s);
@@ -490,6 +502,15 @@ static int build_impl(mls_ctx* ctx, mls_transfer* T, const void* x, const void* 
 int mls_build_transfer(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M, int32_t method,
                        void* stream) {
   return build_impl(ctx, T, x, area, M, method, stream, nullptr, nullptr);
+}
+
+int mls_build_direct_forcing(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                             int32_t method, const void* u, const void* Vb, double dt, void* U, void* F, void* f,
+                             void* stream) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) return invalid("mls_build_direct_forcing: dt must be positive and finite");
+  if (M > 0 && (!u || !Vb || !F || !f)) return invalid("mls_build_direct_forcing: NULL field, velocity or force");
+  if (M == 0) return build_impl(ctx, T, x, area, M, method, stream, nullptr, nullptr);
+  return build_impl(ctx, T, x, area, M, method, stream, u, U, Vb, dt, F, f);
 }
 
 int mls_build_interpolate(mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M, int32_t method,

@@ -136,8 +136,11 @@ cudaError_t launch_build_exact(const mls_ctx* ctx, mls_transfer* T, const void* 
                                cudaStream_t s);
 cudaError_t launch_build_fast(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                               cudaStream_t s);
+// The exact build with the interpolation fused in; with F, also the direct
+// forcing F = (Vb - U) / dt (U may then be nullptr).
 cudaError_t launch_build_exact_interp(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area,
-                                      int64_t M, const void* u, void* U, cudaStream_t s);
+                                      int64_t M, const void* u, void* U, cudaStream_t s, const void* Vb = nullptr,
+                                      double dt = 0.0, void* F = nullptr);
 cudaError_t launch_fast_table(mls_ctx* ctx, cudaStream_t s);
 cudaError_t launch_direct_forcing(const mls_ctx* ctx, const mls_transfer* T, const void* u, const void* Vb,
                                   double dt, void* U, void* F, void* f, cudaStream_t s);
