@@ -97,7 +97,9 @@ typedef struct {
 
 /* Device views into a built transfer (borrowed; valid until the next build on
  * the handle or its destruction).  Markers are stored in "tile order", a
- * permutation of the caller's order that groups markers by spreading tile. */
+ * permutation of the caller's order that groups markers by spreading tile
+ * and, inside a tile of at most 2^12 cells, by home cell (the order among
+ * markers of one home cell is not fixed). */
 typedef struct {
   int64_t M;             /* markers in the last build */
   const void* phi;       /* device, real[27][capacity]: phi[k][j] for stored marker j (Eq. 6 / Eq. 9) */

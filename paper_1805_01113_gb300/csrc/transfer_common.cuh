@@ -175,8 +175,8 @@ __device__ __forceinline__ int round_mul(float a, float b) {
 // Adds one marker's 27 x 3 fixed-point terms round(phi_k q_c) into the shared
 // accumulator, a0 pointing at the stencil's (-1,-1,-1) cell, rows AX cells
 // apart, planes PS, components ACC.  Markers of one warp often share a home
-// cell (tile order follows the caller's surface order), and lanes that add to
-// one word in the same instruction are serialised.  So each lane walks the
+// cell (inside a tile, markers are ordered by home cell), and lanes that add
+// to one word in the same instruction are serialised.  So each lane walks the
 // stencil in its own order: x rotated by lane % 3 and z by (lane / 3) % 3;
 // at step (cz, cy, cx) the lane adds node ((cz + rc) % 3, cy, (cx + ra) % 3).
 // The integer sums do not depend on the order.
