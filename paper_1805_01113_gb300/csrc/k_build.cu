@@ -231,11 +231,11 @@ __device__ __forceinline__ void fast_marker(const BuildArgs<R>& a, int64_t j, co
   const int cl = a.class_axis >= 0 ? h[a.class_axis] : 0;
   const R* T = table + ((int64_t)cl * n * n * n + (int64_t)(((sc[2] * n) + sc[1]) * n + sc[0])) * kTableRow;
   // Corner q sits at sub-node offset (q&1, (q>>1)&1, q>>2) from the sub-cell origin.
-  int64_t roff[8];
+  int roff[8];   // within one class's table: n^3 kTableRow values, far below 2^31
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     alpha[q] *= inv;
-    roff[q] = (int64_t)((((q >> 2) * n) + ((q >> 1) & 1)) * n + (q & 1)) * kTableRow;
+    roff[q] = ((((q >> 2) * n) + ((q >> 1) & 1)) * n + (q & 1)) * kTableRow;
   }
   // Rows are kTableRow = 28 values (27 + one pad), 16-byte aligned: read in
   // 16-byte vectors, kTableRow / kVec of them per corner.

@@ -25,16 +25,17 @@ struct ForceSmem {
 // U_l = sum_k phi_k^l u_k, F_l = (V_b,l - U_l) / dt, f_k += sum_l c_l phi_k^l F_l.
 // Persistent blocks walk the non-empty spreading tiles.  For a tile, every
 // marker flags the 9 rows (y, z) its support touches; the flagged rows of u
-// are copied into a shared-memory brick; then per chunk of up to 128 markers
-// each thread loads its marker's 27 phi once, gathers U from the brick, forms
-// F (written to F and, if requested, U in caller order) and adds c phi F into
-// the int32 fixed-point accumulator exactly as k_spread does (per-component
-// power-of-two scale per chunk, |phi| > 1/2 terms and non-finite chunks
+// are copied into a shared-memory brick; then per chunk of up to
+// kForceThreads (256) markers each thread loads its marker's 27 phi once,
+// gathers U from the brick, forms F (written to F and, if requested, U in
+// caller order) and adds c phi F into the int32 fixed-point accumulator as
+// k_spread does (per-component power-of-two scale per chunk, so that a cell
+// sum stays below 256 * 2^22 = 2^30; |phi| > 1/2 terms and non-finite chunks
 // added directly); the flagged rows are flushed with vector reductions (VEC)
 // or scalar atomics and reset.  Markers without support (the last bin of the
 // tile sort) get U = F = 0.
 template <typename FT, bool VEC, int LX, int LY = 0, int LZ = 0>
-__global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
+__global__ void __launch_bounds__(kForceThreads) k_direct_forcing(
     Dims D, Tiles tl, const float* __restrict__ phi, const float* __restrict__ cl, const int32_t* __restrict__ home,
     const int32_t* __restrict__ perm, const int32_t* __restrict__ items, const int32_t* __restrict__ n_items_p,
     const int32_t* __restrict__ offsets, const int32_t* __restrict__ counts, int64_t M, int64_t cap,
@@ -56,12 +57,12 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
   int* row_s = row_a + ROWS;
   int* row_g = row_s + ROWS;
   unsigned char* flag = reinterpret_cast<unsigned char*>(row_g + ROWS);
-  __shared__ float s_red[3 * (kSpreadThreads / 32)];
+  __shared__ float s_red[3 * (kForceThreads / 32)];
   const int tid = threadIdx.x;
   const int64_t N = (int64_t)D.n[0] * D.n[1] * D.n[2];
   const int n_items = *n_items_p;
-  for (int e = tid; e < 3 * ACC; e += kSpreadThreads) acc[e] = 0;
-  for (int r = tid; r < ROWS; r += kSpreadThreads) flag[r] = 0;
+  for (int e = tid; e < 3 * ACC; e += kForceThreads) acc[e] = 0;
+  for (int r = tid; r < ROWS; r += kForceThreads) flag[r] = 0;
   __syncthreads();
 
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
     const int bx = b % tl.nb[0], by = (b / tl.nb[0]) % tl.nb[1], bz = b / (tl.nb[0] * tl.nb[1]);
     const int ox = bx << LX, oy = by << ly, oz = bz << lz;
     // Touched rows of the whole tile (plain byte stores) and the row tables.
-    for (int j = start + tid; j < end; j += kSpreadThreads) {
+    for (int j = start + tid; j < end; j += kForceThreads) {
       int i[3];
       decode_home(home[j], D, i);
       const int r0 = (i[2] - oz) * AY + (i[1] - oy);
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
 #pragma unroll
         for (int cy = 0; cy < 3; ++cy) flag[r0 + cz * AY + cy] = 1;
     }
-    for (int r = tid; r < ROWS; r += kSpreadThreads) {
+    for (int r = tid; r < ROWS; r += kForceThreads) {
       const int ey = r % AY, ez = r / AY;
       row_a[r] = ez * PS + ey * AX;
       row_s[r] = ez * BPS + ey * BX;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
     }
     __syncthreads();
     // The touched rows of u into the brick.
-    for (int e = tid; e < ROWS * BX; e += kSpreadThreads) {
+    for (int e = tid; e < ROWS * BX; e += kForceThreads) {
       const int r = e / BX, ex = e - r * BX;
       if (!flag[r]) continue;
       const int gx = wrap(ox - 1 + ex, D.n[0], D.periodic[0]);
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
     cp_async_wait_all();
     __syncthreads();
 
-    for (int j0 = start; j0 < end; j0 += kSpreadThreads) {
+    for (int j0 = start; j0 < end; j0 += kForceThreads) {
       const int64_t j = j0 + tid;
       const bool act = j < end;
       int i[3] = {0, 0, 0};
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
         v[2] = c * F2;
       }
       float vm[3] = {fabsf(v[0]), fabsf(v[1]), fabsf(v[2])};
-      block_max3(vm, s_red);
+      block_max3<kForceThreads>(vm, s_red);
       const float vmax = fmaxf(vm[0], fmaxf(vm[1], vm[2]));
       if (vmax == 0.f) {
         __syncthreads();
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
       __syncthreads();
       if (VEC) {
         constexpr int G = AX / 4;
-        for (int g = tid; g < G * ROWS; g += kSpreadThreads) {
+        for (int g = tid; g < G * ROWS; g += kForceThreads) {
           const int row = g / G, q = g - row * G;
           if (!flag[row]) continue;
           const int e = row_a[row] + 4 * q;
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
           if (n2) red_add_v4(fo + 2 * N, a2.x * u2, a2.y * u2, a2.z * u2, a2.w * u2);
         }
       } else {
-        for (int e = tid; e < AX * ROWS; e += kSpreadThreads) {
+        for (int e = tid; e < AX * ROWS; e += kForceThreads) {
           const int row = e / AX, ex = e - row * AX;
           if (!flag[row]) continue;
           const int li = row_a[row] + ex;
@@ -244,13 +245,13 @@ __global__ void __launch_bounds__(kSpreadThreads) k_direct_forcing(
     }
     // The tile's flags are cleared once all its chunks are flushed; the next
     // tile sets its own only after the barrier.
-    for (int r = tid; r < ROWS; r += kSpreadThreads) flag[r] = 0;
+    for (int r = tid; r < ROWS; r += kForceThreads) flag[r] = 0;
     __syncthreads();
   }
   // Markers without support: no interpolated velocity and no force.
   const int64_t d0 = offsets[tl.nbins - 1];
-  for (int64_t j = d0 + (int64_t)blockIdx.x * kSpreadThreads + tid; j < M;
-       j += (int64_t)gridDim.x * kSpreadThreads) {
+  for (int64_t j = d0 + (int64_t)blockIdx.x * kForceThreads + tid; j < M;
+       j += (int64_t)gridDim.x * kForceThreads) {
     const int64_t m = perm[j];
     if (U) {
       U[m] = 0.f;
@@ -308,7 +309,7 @@ static cudaError_t force_configure_one(mls_ctx* ctx, const void* k, int smem) {
   if ((e = raise_smem_limit(k, smem)) != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSpreadThreads, smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kForceThreads, smem)) != cudaSuccess) return e;
   ctx->force_grid = (per_sm > 0 ? per_sm : 1) * sms;
   return cudaSuccess;
 }
@@ -369,7 +370,7 @@ cudaError_t launch_direct_forcing(const mls_ctx* ctx, const mls_transfer* T, con
   void* args[] = {&D, &tl, (void*)&phi, (void*)&c, (void*)&T->home, (void*)&T->perm, (void*)&T->items,
                   (void*)&T->n_items, (void*)&T->offsets, (void*)&T->counts, &M, &cap, (void*)&u, (void*)&Vb,
                   &inv_dt, &U, &F, &f};
-  return cudaLaunchKernel(k, dim3(ctx->force_grid), dim3(kSpreadThreads), args, force_smem_bytes(ctx), s);
+  return cudaLaunchKernel(k, dim3(ctx->force_grid), dim3(kForceThreads), args, force_smem_bytes(ctx), s);
 }
 
 }  // namespace mls

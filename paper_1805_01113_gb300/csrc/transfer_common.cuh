@@ -144,6 +144,7 @@ struct SpreadSmem {
   }
 };
 
+template <int NT = kSpreadThreads>
 __device__ __forceinline__ void block_max3(float v[3], float* red) {
 #pragma unroll
   for (int q = 0; q < 3; ++q)
@@ -159,7 +160,7 @@ __device__ __forceinline__ void block_max3(float v[3], float* red) {
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     float m = red[q];
-    for (int ww = 1; ww < kSpreadThreads / 32; ++ww) m = fmaxf(m, red[3 * ww + q]);
+    for (int ww = 1; ww < NT / 32; ++ww) m = fmaxf(m, red[3 * ww + q]);
     v[q] = m;
   }
 }

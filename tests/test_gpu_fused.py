@@ -135,17 +135,38 @@ def test_fused_bf16_field(api):
     assert normwise(g["U"], r["U"]) <= TOL["f32"]
 
 
-@pytest.mark.parametrize("method", ["fast", "exact-quadratic"])
-def test_fused_other_forms_run_both_calls(api, method):
-    """Fast-MLS and the quadratic basis: the call equals build_transfer + interpolate."""
+def test_fused_quadratic_runs_both_calls(api):
+    """The quadratic exact basis: the call equals build_transfer + interpolate."""
     w = make_workload("c2", n=64, n_bodies=8)
     x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
     ut = torch.as_tensor(field_full_np(w.modes, w.faces, np.float32), device=DEV)
-    basis = 10 if method == "exact-quadratic" else 4
-    m = "exact" if method == "exact-quadratic" else "fast"
-    ctx = api.Context(w.faces, w.periodic, real="f32", basis=basis)
-    g = _fused(ctx, x, area, ut, method=m)
-    s = run_gpu(ctx, x, area, m, ut)
+    ctx = api.Context(w.faces, w.periodic, real="f32", basis=10)
+    g = _fused(ctx, x, area, ut, method="exact")
+    s = run_gpu(ctx, x, area, "exact", ut)
+    assert np.array_equal(g["U"], s["U"])
+    _check_against_separate(g, s, 0.0)
+
+
+@pytest.mark.parametrize("case", ["uniform", "stretched", "bf16", "f64", "quadratic"])
+def test_fused_fast(api, case):
+    """Fast-MLS (table in shared memory on the uniform grid, read through the cache on the
+    stretched one) runs the two calls in turn: the same transfer and U."""
+    if case == "f64":
+        w = make_workload("c1", n=32, level=3, radius=0.3)
+        x, area = oracle.marker_prep(w.vertices, w.tri, "f64")
+        ut = torch.as_tensor(field_full_np(w.modes, w.faces), device=DEV)
+        ctx = api.Context(w.faces, w.periodic, real="f64")
+    else:
+        w = make_workload("c3", n=96, n_bodies=16) if case == "stretched" else make_workload("c2", n=64, n_bodies=12)
+        x, area = oracle.marker_prep(w.vertices.astype(np.float32), w.tri, "f32")
+        ut = torch.as_tensor(field_full_np(w.modes, w.faces, np.float32), device=DEV)
+        if case == "bf16":
+            ut = ut.to(torch.bfloat16)
+        ctx = api.Context(w.faces, w.periodic, real="f32", field="bf16" if case == "bf16" else "f32",
+                          basis=10 if case == "quadratic" else 4)
+    g = _fused(ctx, x, area, ut, method="fast")
+    s = run_gpu(ctx, x, area, "fast", ut)
+    assert g["status"]["dropped"] == 0
     assert np.array_equal(g["U"], s["U"])
     _check_against_separate(g, s, 0.0)
 
