@@ -45,6 +45,8 @@ cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri,
   return cudaGetLastError();
 }
 
+constexpr int kLocatePer = 4;   // rounds of 32 markers per warp of the locate kernel
+
 // Home cell of every marker, its spreading-tile bin, and its rank inside the
 // bin (warp-aggregated atomic counter per bin).  Dropped markers go to the
 // last bin and are counted in status[0] (all) and status[1] (non-finite).
@@ -55,35 +57,62 @@ __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R*
                                                    int32_t* __restrict__ counts,
                                                    unsigned long long* __restrict__ status,
                                                    int32_t* __restrict__ sub) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= M) return;
-  const R p[3] = {x[j], x[M + j], x[2 * M + j]};
-  const R ar = area[j];
-  const bool finite = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(ar);
-  bool ok = finite;
-  int h[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    h[d] = locate_axis(g.ax[d], p[d]);
-    ok = ok && support_ok(g.ax[d], h[d]);
-  }
-  int k = tl.nbins - 1;
-  if (ok)
-    k = (((h[2] >> tl.l[2]) * tl.nb[1]) + (h[1] >> tl.l[1])) * tl.nb[0] + (h[0] >> tl.l[0]);
-  const unsigned peers = __match_any_sync(__activemask(), k);
+  // A warp takes kLocatePer rounds of 32 consecutive markers; every round's
+  // loads, then every round's bin counter update, are issued before any
+  // result is waited for.
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(&counts[k], __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  key[j] = k;
-  rank[j] = base + __popc(peers & ((1u << lane) - 1u));
-  if (sub && ok)
-    sub[j] = ((((h[2] & ((1 << tl.l[2]) - 1)) << tl.l[1]) | (h[1] & ((1 << tl.l[1]) - 1))) << tl.l[0]) |
-             (h[0] & ((1 << tl.l[0]) - 1));
-  if (!ok) {
-    atomicAdd(&status[0], 1ULL);
-    if (!finite) atomicAdd(&status[1], 1ULL);
+  const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kLocatePer);
+  R p[kLocatePer][3], ar[kLocatePer];
+#pragma unroll
+  for (int r = 0; r < kLocatePer; ++r) {
+    const int64_t j = w0 + r * 32 + lane;
+    if (j < M) {
+      p[r][0] = x[j];
+      p[r][1] = x[M + j];
+      p[r][2] = x[2 * M + j];
+      ar[r] = area[j];
+    }
+  }
+  int k[kLocatePer], cell[kLocatePer];
+  unsigned peers[kLocatePer];
+  int base[kLocatePer];
+#pragma unroll
+  for (int r = 0; r < kLocatePer; ++r) {
+    const int64_t j = w0 + r * 32 + lane;
+    k[r] = -1;   // no marker: a group of its own that counts nothing
+    cell[r] = 0;
+    if (j < M) {
+      const bool finite = isfinite(p[r][0]) && isfinite(p[r][1]) && isfinite(p[r][2]) && isfinite(ar[r]);
+      bool ok = finite;
+      int h[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        h[d] = locate_axis(g.ax[d], p[r][d]);
+        ok = ok && support_ok(g.ax[d], h[d]);
+      }
+      k[r] = tl.nbins - 1;
+      if (ok) {
+        k[r] = (((h[2] >> tl.l[2]) * tl.nb[1]) + (h[1] >> tl.l[1])) * tl.nb[0] + (h[0] >> tl.l[0]);
+        cell[r] = ((((h[2] & ((1 << tl.l[2]) - 1)) << tl.l[1]) | (h[1] & ((1 << tl.l[1]) - 1))) << tl.l[0]) |
+                  (h[0] & ((1 << tl.l[0]) - 1));
+      } else {
+        atomicAdd(&status[0], 1ULL);
+        if (!finite) atomicAdd(&status[1], 1ULL);
+      }
+    }
+    peers[r] = __match_any_sync(0xffffffffu, k[r]);
+    base[r] = 0;
+    if (k[r] >= 0 && lane == __ffs(peers[r]) - 1) base[r] = atomicAdd(&counts[k[r]], __popc(peers[r]));
+  }
+#pragma unroll
+  for (int r = 0; r < kLocatePer; ++r) {
+    const int64_t j = w0 + r * 32 + lane;
+    const int b = __shfl_sync(0xffffffffu, base[r], __ffs(peers[r]) - 1);
+    if (j < M) {
+      key[j] = k[r];
+      rank[j] = b + __popc(peers[r] & ((1u << lane) - 1u));
+      if (sub && k[r] != tl.nbins - 1) sub[j] = cell[r];
+    }
   }
 }
 
@@ -98,7 +127,7 @@ bool tile_sort_on(const mls_ctx* ctx) {
 
 cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                           cudaStream_t s) {
-  const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  const unsigned grid = (unsigned)((M + kBlock * kLocatePer - 1) / (kBlock * kLocatePer));
   int32_t* sub = tile_sort_on(ctx) ? reinterpret_cast<int32_t*>(T->phi) : nullptr;
   if (ctx->opt.real == MLS_F64)
     k_locate<double><<<grid, kBlock, 0, s>>>(device_grid<double>(ctx), ctx->tiles, (const double*)x,
@@ -226,15 +255,32 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t* __restrict__ 
                                                     const int32_t* __restrict__ offsets, int64_t M,
                                                     int32_t* __restrict__ perm, const int32_t* __restrict__ sub,
                                                     int32_t* __restrict__ cell) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= M) return;
-  const int64_t pos = offsets[key[j]] + rank[j];
-  perm[pos] = (int32_t)j;
-  if (cell) cell[pos] = sub[j];
+  // kLocatePer markers per thread, a block's in consecutive strides, so that
+  // the loads of all of them are in flight before the first store.
+  const int64_t j0 = (int64_t)blockIdx.x * blockDim.x * kLocatePer + threadIdx.x;
+  int64_t pos[kLocatePer];
+  int cl[kLocatePer];
+#pragma unroll
+  for (int r = 0; r < kLocatePer; ++r) {
+    const int64_t j = j0 + (int64_t)r * blockDim.x;
+    pos[r] = -1;
+    if (j < M) {
+      pos[r] = offsets[key[j]] + rank[j];
+      if (cell) cl[r] = sub[j];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kLocatePer; ++r) {
+    const int64_t j = j0 + (int64_t)r * blockDim.x;
+    if (pos[r] >= 0) {
+      perm[pos[r]] = (int32_t)j;
+      if (cell) cell[pos[r]] = cl[r];
+    }
+  }
 }
 
 cudaError_t launch_scatter(const mls_ctx* ctx, mls_transfer* T, int64_t M, cudaStream_t s) {
-  const unsigned grid = (unsigned)((M + kBlock - 1) / kBlock);
+  const unsigned grid = (unsigned)((M + kBlock * kLocatePer - 1) / (kBlock * kLocatePer));
   if (tile_sort_on(ctx))
     k_scatter<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->home,
                                       reinterpret_cast<const int32_t*>(T->phi), reinterpret_cast<int32_t*>(T->c));
