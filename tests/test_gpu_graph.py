@@ -31,7 +31,11 @@ def api():
     return _api
 
 
-def test_graph_replay_on_new_positions_and_forces(api):
+@pytest.mark.parametrize("calls", ["separate", "build_interpolate", "build_direct_forcing"])
+def test_graph_replay_on_new_positions_and_forces(api, calls):
+    """The step through the three calls, through mls_build_interpolate (the
+    benchmark's headline), and the direct-forcing step through
+    mls_build_direct_forcing (forces F = (V_b - U)/dt)."""
     w = make_workload("c3", n=96, n_bodies=16)
     grid = oracle.Grid(w.faces, w.periodic)
     M = w.n_markers
@@ -48,12 +52,22 @@ def test_graph_replay_on_new_positions_and_forces(api):
     f = torch.zeros_like(u)
     T = ctx.transfer(M)
 
+    Vb = torch.zeros((3, M), dtype=torch.float32, device=DEV)
+    Fo = torch.empty((3, M), dtype=torch.float32, device=DEV)
+    dt = 0.5
+
     def step():
         f.zero_()
         ctx.marker_prep(V, tri, x, area)
-        ctx.build_transfer(T, x, area, "exact")
-        ctx.interpolate(T, u, U)
-        ctx.spread(T, F, f)
+        if calls == "separate":
+            ctx.build_transfer(T, x, area, "exact")
+            ctx.interpolate(T, u, U)
+            ctx.spread(T, F, f)
+        elif calls == "build_interpolate":
+            ctx.build_interpolate(T, x, area, u, U, method="exact")
+            ctx.spread(T, F, f)
+        else:
+            ctx.build_direct_forcing(T, x, area, u, Vb, dt, f, F=Fo, U=U, method="exact")
 
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -79,8 +93,10 @@ def test_graph_replay_on_new_positions_and_forces(api):
             Vn[vids] += shift[b]
         Vn = Vn.astype(np.float32)
         Fn = rng.normal(size=(3, M)).astype(np.float32)
+        Vbn = rng.normal(size=(3, M)).astype(np.float32)
         V.copy_(torch.as_tensor(Vn))
         F.copy_(torch.as_tensor(Fn))
+        Vb.copy_(torch.as_tensor(Vbn))
         g.replay()
         torch.cuda.synchronize()
         assert ctx.status(T)["dropped"] == 0
@@ -89,7 +105,13 @@ def test_graph_replay_on_new_positions_and_forces(api):
         tr = oracle.shape_exact(grid, xr, 1.0)
         c = oracle.forcing_scale(tr, ar)
         U_ref = oracle.interpolate(tr, u_np.astype(np.float64))
-        f_ref = oracle.spread(tr, c, Fn.astype(np.float64), grid.n).to_dense(grid.n)
+        if calls == "build_direct_forcing":
+            U_ref, F_ref, sp = oracle.direct_forcing(tr, c, u_np.astype(np.float64), Vbn.astype(np.float64), dt,
+                                                     grid.n)
+            f_ref = sp.to_dense(grid.n)
+            assert normwise(Fo.double().cpu().numpy(), F_ref) <= TOL
+        else:
+            f_ref = oracle.spread(tr, c, Fn.astype(np.float64), grid.n).to_dense(grid.n)
         assert normwise(U.double().cpu().numpy(), U_ref) <= TOL
         fg = f.double().cpu().numpy()
         assert normwise(fg, f_ref) <= TOL
