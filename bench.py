@@ -468,7 +468,9 @@ def run_ours(a, rank, world, local):
 
     # per-kernel pass (events around each kernel on the launching stream)
     ms_k, kt = timed(a.method, a.steps, 2, True)
-    launches = sum(n for k, (n, _) in kt.items() if k != "bin_reset")
+    # kernels per timed phase: the exact builds also launch their double re-solve kernel
+    per_phase = {"build_exact": 2, "build_exact_interp": 2, "build_exact_forcing": 2}
+    launches = sum(n * per_phase.get(k, 1) for k, (n, _) in kt.items() if k != "bin_reset")
     per_launch = {k: tot / n for k, (n, tot) in kt.items() if n}
     dom = max((k for k in per_launch if k != "bin_reset"), key=lambda k: kt[k][1])
     pk, pk_src = peaks()
