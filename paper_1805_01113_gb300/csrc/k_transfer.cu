@@ -215,7 +215,7 @@ static const void* interp_kernel(int lx) {
 // (zero lanes of a group add nothing).  A chunk with non-finite forces is
 // added directly.
 template <typename FT, bool VEC, int LX, int LY = 0, int LZ = 0>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(Dims D, Tiles tl, const float* __restrict__ phi,
+__global__ void __launch_bounds__(kSpreadThreads, 8) k_spread(Dims D, Tiles tl, const float* __restrict__ phi,
                                                            const float* __restrict__ cl,
                                                            const int32_t* __restrict__ home,
                                                            const int32_t* __restrict__ perm,
