@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmls_gb300.so")
-SOURCES = ["mls_api.cu", "k_prep_sort.cu", "k_build.cu", "k_transfer.cu", "k_force.cu", "k_collision.cu", "k_refine.cu",
+SOURCES = ["mls_api.cu", "k_prep_sort.cu", "k_build.cu", "k_transfer.cu", "k_force.cu", "k_force_256.cu", "k_collision.cu", "k_refine.cu",
            "k_gradient.cu",
            "mls_noalloc.cu",
            "k_mlp.cu", "mls_surrogate_api.cu", "mls_checkpoint.cu"]

@@ -45,26 +45,30 @@ cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri,
   return cudaGetLastError();
 }
 
-constexpr int kLocatePer = 4;   // rounds of 32 markers per warp of the locate kernel
+// Markers per thread of the locate and scatter kernels: 4 on workloads that
+// fill the GPU several times over (their loads then overlap), 1 on small ones
+// (which need every block they can get).
+constexpr int kLocatePer = 4;
+inline int locate_per(int64_t M) { return M >= (int64_t)kLocatePer * 152 * 2048 ? kLocatePer : 1; }
 
 // Home cell of every marker, its spreading-tile bin, and its rank inside the
 // bin (warp-aggregated atomic counter per bin).  Dropped markers go to the
 // last bin and are counted in status[0] (all) and status[1] (non-finite).
-template <typename R>
+template <typename R, int PER>
 __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R* __restrict__ x,
                                                    const R* __restrict__ area, int64_t M,
                                                    int32_t* __restrict__ key, int32_t* __restrict__ rank,
                                                    int32_t* __restrict__ counts,
                                                    unsigned long long* __restrict__ status,
                                                    int32_t* __restrict__ sub) {
-  // A warp takes kLocatePer rounds of 32 consecutive markers; every round's
+  // A warp takes PER rounds of 32 consecutive markers; every round's
   // loads, then every round's bin counter update, are issued before any
   // result is waited for.
   const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kLocatePer);
-  R p[kLocatePer][3], ar[kLocatePer];
+  const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * PER);
+  R p[PER][3], ar[PER];
 #pragma unroll
-  for (int r = 0; r < kLocatePer; ++r) {
+  for (int r = 0; r < PER; ++r) {
     const int64_t j = w0 + r * 32 + lane;
     if (j < M) {
       p[r][0] = x[j];
@@ -73,11 +77,11 @@ __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R*
       ar[r] = area[j];
     }
   }
-  int k[kLocatePer], cell[kLocatePer];
-  unsigned peers[kLocatePer];
-  int base[kLocatePer];
+  int k[PER], cell[PER];
+  unsigned peers[PER];
+  int base[PER];
 #pragma unroll
-  for (int r = 0; r < kLocatePer; ++r) {
+  for (int r = 0; r < PER; ++r) {
     const int64_t j = w0 + r * 32 + lane;
     k[r] = -1;   // no marker: a group of its own that counts nothing
     cell[r] = 0;
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R*
     if (k[r] >= 0 && lane == __ffs(peers[r]) - 1) base[r] = atomicAdd(&counts[k[r]], __popc(peers[r]));
   }
 #pragma unroll
-  for (int r = 0; r < kLocatePer; ++r) {
+  for (int r = 0; r < PER; ++r) {
     const int64_t j = w0 + r * 32 + lane;
     const int b = __shfl_sync(0xffffffffu, base[r], __ffs(peers[r]) - 1);
     if (j < M) {
@@ -127,14 +131,17 @@ bool tile_sort_on(const mls_ctx* ctx) {
 
 cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                           cudaStream_t s) {
-  const unsigned grid = (unsigned)((M + kBlock * kLocatePer - 1) / (kBlock * kLocatePer));
+  const int per = locate_per(M);
+  const unsigned grid = (unsigned)((M + kBlock * per - 1) / (kBlock * per));
   int32_t* sub = tile_sort_on(ctx) ? reinterpret_cast<int32_t*>(T->phi) : nullptr;
   if (ctx->opt.real == MLS_F64)
-    k_locate<double><<<grid, kBlock, 0, s>>>(device_grid<double>(ctx), ctx->tiles, (const double*)x,
-                                             (const double*)area, M, T->key, T->rank, T->counts, T->status, sub);
+    (per == kLocatePer ? k_locate<double, kLocatePer> : k_locate<double, 1>)<<<grid, kBlock, 0, s>>>(
+        device_grid<double>(ctx), ctx->tiles, (const double*)x, (const double*)area, M, T->key, T->rank, T->counts,
+        T->status, sub);
   else
-    k_locate<float><<<grid, kBlock, 0, s>>>(device_grid<float>(ctx), ctx->tiles, (const float*)x,
-                                            (const float*)area, M, T->key, T->rank, T->counts, T->status, sub);
+    (per == kLocatePer ? k_locate<float, kLocatePer> : k_locate<float, 1>)<<<grid, kBlock, 0, s>>>(
+        device_grid<float>(ctx), ctx->tiles, (const float*)x, (const float*)area, M, T->key, T->rank, T->counts,
+        T->status, sub);
   return cudaGetLastError();
 }
 
@@ -251,17 +258,18 @@ cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx
 // perm[offsets[bin] + rank] = caller index: stable within nothing, grouped by
 // bin.  With the in-tile sort, the caller index and the marker's cell in its
 // tile go to the sort's scratch arrays instead (`perm` unsorted, `cell`).
+template <int PER>
 __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t* __restrict__ key, const int32_t* __restrict__ rank,
                                                     const int32_t* __restrict__ offsets, int64_t M,
                                                     int32_t* __restrict__ perm, const int32_t* __restrict__ sub,
                                                     int32_t* __restrict__ cell) {
-  // kLocatePer markers per thread, a block's in consecutive strides, so that
+  // PER markers per thread, a block's in consecutive strides, so that
   // the loads of all of them are in flight before the first store.
-  const int64_t j0 = (int64_t)blockIdx.x * blockDim.x * kLocatePer + threadIdx.x;
-  int64_t pos[kLocatePer];
-  int cl[kLocatePer];
+  const int64_t j0 = (int64_t)blockIdx.x * blockDim.x * PER + threadIdx.x;
+  int64_t pos[PER];
+  int cl[PER];
 #pragma unroll
-  for (int r = 0; r < kLocatePer; ++r) {
+  for (int r = 0; r < PER; ++r) {
     const int64_t j = j0 + (int64_t)r * blockDim.x;
     pos[r] = -1;
     if (j < M) {
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t* __restrict__ 
     }
   }
 #pragma unroll
-  for (int r = 0; r < kLocatePer; ++r) {
+  for (int r = 0; r < PER; ++r) {
     const int64_t j = j0 + (int64_t)r * blockDim.x;
     if (pos[r] >= 0) {
       perm[pos[r]] = (int32_t)j;
@@ -280,12 +288,14 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t* __restrict__ 
 }
 
 cudaError_t launch_scatter(const mls_ctx* ctx, mls_transfer* T, int64_t M, cudaStream_t s) {
-  const unsigned grid = (unsigned)((M + kBlock * kLocatePer - 1) / (kBlock * kLocatePer));
+  const int per = locate_per(M);
+  const unsigned grid = (unsigned)((M + kBlock * per - 1) / (kBlock * per));
+  auto k = per == kLocatePer ? k_scatter<kLocatePer> : k_scatter<1>;
   if (tile_sort_on(ctx))
-    k_scatter<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->home,
-                                      reinterpret_cast<const int32_t*>(T->phi), reinterpret_cast<int32_t*>(T->c));
+    k<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->home, reinterpret_cast<const int32_t*>(T->phi),
+                              reinterpret_cast<int32_t*>(T->c));
   else
-    k_scatter<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->perm, nullptr, nullptr);
+    k<<<grid, kBlock, 0, s>>>(T->key, T->rank, T->offsets, M, T->perm, nullptr, nullptr);
   return cudaGetLastError();
 }
 

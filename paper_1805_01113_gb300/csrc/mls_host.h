@@ -89,8 +89,8 @@ constexpr int kBlock = 256;           // threads per block of the per-marker ker
 constexpr int kBlockF64 = 64;         // the same for the double-precision builds and gradient (FP64-bound:
                                       // small workloads should spread over many SMs)
 constexpr int kSpreadThreads = 128;   // threads per block of the spreading kernel
-constexpr int kForceThreads = 256;    // threads per block of the fused direct-forcing pass (3.87 against
-                                      // 4.21 ms with 128 on 32 M markers; the spread alone is faster with 128)
+constexpr int kForceThreads = 256;    // threads per block of the fused direct-forcing pass on tiles of at least
+                                      // 2^9 cells (smaller tiles: kSpreadThreads)
 constexpr int kTableRow = 28;         // fast-MLS table row: 27 shape-function values + 1 pad (16-byte rows)
 constexpr int kInterpThreads = 128;   // threads per block of the tile-organised interpolation
 constexpr int kSortThreads = 256;     // threads per block of the in-tile sort (a warp per tile)
