@@ -643,22 +643,41 @@ def run_ours(a, rank, world, local):
     if not a.no_e2e:
         U_host = torch.empty((3, M), dtype=tdt).pin_memory()
         # The library's calls are stream-ordered, so the copies overlap the
-        # kernels that do not need them: F goes up on a copy stream (after the
-        # vertices) while the build and interpolation run, and U comes down on
-        # the copy stream while the spread runs.
+        # kernels that do not need them.  The vertices go up on a copy stream
+        # in pieces of whole bodies, and each piece's markers are prepared as
+        # soon as it lands (mls_marker_prep_range) while the next piece is
+        # copied; F follows on the copy stream while the build and
+        # interpolation run, and U comes down on it while the spread runs.
         cstream = torch.cuda.Stream(device=dev)
-        ev_v, ev_f, ev_u = (torch.cuda.Event() for _ in range(3))
+        ev_f, ev_u = torch.cuda.Event(), torch.cuda.Event()
+        n_pieces = 8
+        bf = np.asarray(w.body_faces)
+        cut_b = sorted({int(np.searchsorted(bf, M * q // n_pieces)) for q in range(1, n_pieces)} | {len(bf) - 1})
+        pieces, t0, v0 = [], 0, 0
+        for b in cut_b:
+            t1 = int(bf[min(b, len(bf) - 1)])
+            if t1 <= t0:
+                continue
+            v1 = int(w.tri[:t1].max()) + 1
+            pieces.append((t0, t1, v0, max(v0, v1)))
+            t0, v0 = t1, max(v0, v1)
+        if v0 < V.shape[0]:                                 # vertices no triangle refers to
+            t_last, _, v_last, _ = pieces[-1]
+            pieces[-1] = (t_last, M, v_last, V.shape[0])
+        ev_v = [torch.cuda.Event() for _ in pieces]
 
         def e2e_step():
             stream = torch.cuda.current_stream()       # the capture stream while a graph is captured
             cstream.wait_stream(stream)
-            V.copy_(V_host, non_blocking=True)
-            ev_v.record(stream)
             with torch.cuda.stream(cstream):
-                cstream.wait_event(ev_v)
+                for (_, _, v0, v1), ev in zip(pieces, ev_v):
+                    V[v0:v1].copy_(V_host[v0:v1], non_blocking=True)
+                    ev.record(cstream)
                 F.copy_(F_host, non_blocking=True)
                 ev_f.record(cstream)
-            ctx.marker_prep(V, tri, x, area)
+            for (t0, t1, _, _), ev in zip(pieces, ev_v):
+                stream.wait_event(ev)
+                ctx.marker_prep(V, tri, x, area, begin=t0, end=t1)
             if a.method == "exact":
                 ctx.build_interpolate(T, x, area, u, U, method="exact")
             else:
@@ -690,8 +709,9 @@ def run_ours(a, rank, world, local):
                "d2h_bytes_per_step": U_host.numel() * U_host.element_size(),
                "ms_per_step": 1e3 * statistics.mean(te),
                "ms_per_step_median": 1e3 * statistics.median(te), "ms_per_step_min": 1e3 * min(te),
-               "copies": "pinned host buffers; vertices up first, forces up on a copy stream during build and "
-                         "interpolation, marker velocities down on the copy stream during the spread"}
+               "copies": f"pinned host buffers; vertices up on a copy stream in {len(pieces)} pieces of whole "
+                         "bodies, each piece's markers prepared as it lands; forces up after them during build "
+                         "and interpolation, marker velocities down on the copy stream during the spread"}
         # The same step (copies included) captured once into a CUDA graph and
         # replayed: what a caller that captures its time step gets.
         try:

@@ -153,6 +153,19 @@ int mls_transfer_destroy(mls_transfer* T);
 int mls_marker_prep(mls_ctx* ctx, const void* vertices, int64_t n_vertices,
                     const int32_t* tri, int64_t n_tri, void* x, void* area, void* stream);
 
+/* mls_marker_prep of triangles [t_begin, t_end) only: x[:, t] and area[t]
+ * for t in that range, in the same arrays of n_tri markers (other entries
+ * untouched).  A caller that uploads the vertices in pieces (bodies in
+ * order, each body's triangles referring to its own vertices) can prepare
+ * each piece's markers as soon as its vertices are on the device, while the
+ * next piece is copied; only vertices that the range's triangles refer to
+ * are read.
+ * Errors: MLS_ERR_INVALID_ARG unless 0 <= t_begin <= t_end <= n_tri, on
+ * negative sizes, and on NULL pointers with a non-empty range. */
+int mls_marker_prep_range(mls_ctx* ctx, const void* vertices, int64_t n_vertices,
+                          const int32_t* tri, int64_t n_tri, int64_t t_begin, int64_t t_end,
+                          void* x, void* area, void* stream);
+
 /* Build the transfer functions of M markers into T (Section 2).
  *   x     device, real[3][M] marker positions; area device, real[M] (A_l, Eq. 7)
  *   method MLS_EXACT (Eqs. 3-6), MLS_FAST (Eqs. 9-10; the first fast build

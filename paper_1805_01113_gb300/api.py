@@ -114,7 +114,8 @@ class Context:
     def transfer(self, capacity):
         return Transfer(self, capacity)
 
-    def marker_prep(self, vertices, tri, x=None, area=None, stream=None):
+    def marker_prep(self, vertices, tri, x=None, area=None, stream=None, begin=None, end=None):
+        """Markers of all triangles, or of triangles [begin, end) into the full x and area."""
         nt = tri.shape[0]
         _check_tensor(vertices, "vertices", self.real_t)
         _check_tensor(tri, "tri", torch.int32, (nt, 3))
@@ -126,8 +127,15 @@ class Context:
             area = torch.empty((nt,), dtype=self.real_t, device=vertices.device)
         _check_tensor(x, "x", self.real_t, (3, nt))
         _check_tensor(area, "area", self.real_t, (nt,))
-        B.check(self.lib.mls_marker_prep(self.handle, _ptr(vertices), vertices.shape[0], _ptr(tri), nt,
-                                         _ptr(x), _ptr(area), _stream(stream)), "mls_marker_prep")
+        if begin is None and end is None:
+            B.check(self.lib.mls_marker_prep(self.handle, _ptr(vertices), vertices.shape[0], _ptr(tri), nt,
+                                             _ptr(x), _ptr(area), _stream(stream)), "mls_marker_prep")
+        else:
+            t0 = 0 if begin is None else int(begin)
+            t1 = nt if end is None else int(end)
+            B.check(self.lib.mls_marker_prep_range(self.handle, _ptr(vertices), vertices.shape[0], _ptr(tri), nt,
+                                                   t0, t1, _ptr(x), _ptr(area), _stream(stream)),
+                    "mls_marker_prep_range")
         return x, area
 
     def build_transfer(self, T, x, area, method="exact", stream=None):

@@ -4,16 +4,17 @@
 
 namespace mls {
 
-// Centroid C = ((V1+V2)+V3)/3 and area |(V2-V1)x(V3-V1)|/2 of each triangle,
-// every operation rounded to nearest in R with no contraction, so the result
-// is reproducible bit for bit by any IEEE implementation of the same order.
+// Centroid C = ((V1+V2)+V3)/3 and area |(V2-V1)x(V3-V1)|/2 of triangles
+// [t0, t1) of nt, every operation rounded to nearest in R with no contraction,
+// so the result is reproducible bit for bit by any IEEE implementation of the
+// same order.
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_prep(const R* __restrict__ V, int64_t nv,
-                                                 const int32_t* __restrict__ tri, int64_t nt,
-                                                 R* __restrict__ x, R* __restrict__ area) {
+                                                 const int32_t* __restrict__ tri, int64_t t0, int64_t t1,
+                                                 int64_t nt, R* __restrict__ x, R* __restrict__ area) {
   using O = Ops<R>;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
+  const int64_t t = t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= t1) return;
   const int64_t i0 = tri[3 * t], i1 = tri[3 * t + 1], i2 = tri[3 * t + 2];
   if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
     x[t] = x[nt + t] = x[2 * nt + t] = O::nan_();
@@ -34,14 +35,14 @@ __global__ void __launch_bounds__(kBlock) k_prep(const R* __restrict__ V, int64_
   area[t] = ar;
 }
 
-cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri, int64_t nt, void* x,
-                        void* area, cudaStream_t s) {
-  if (nt == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((nt + kBlock - 1) / kBlock);
+cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri, int64_t t0, int64_t t1,
+                        int64_t nt, void* x, void* area, cudaStream_t s) {
+  if (t1 <= t0) return cudaSuccess;
+  const unsigned grid = (unsigned)((t1 - t0 + kBlock - 1) / kBlock);
   if (real == MLS_F64)
-    k_prep<double><<<grid, kBlock, 0, s>>>((const double*)V, nv, tri, nt, (double*)x, (double*)area);
+    k_prep<double><<<grid, kBlock, 0, s>>>((const double*)V, nv, tri, t0, t1, nt, (double*)x, (double*)area);
   else
-    k_prep<float><<<grid, kBlock, 0, s>>>((const float*)V, nv, tri, nt, (float*)x, (float*)area);
+    k_prep<float><<<grid, kBlock, 0, s>>>((const float*)V, nv, tri, t0, t1, nt, (float*)x, (float*)area);
   return cudaGetLastError();
 }
 

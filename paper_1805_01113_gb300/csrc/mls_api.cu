@@ -346,17 +346,24 @@ int mls_transfer_destroy(mls_transfer* T) {
   return MLS_OK;
 }
 
-int mls_marker_prep(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri, int64_t n_tri,
-                    void* x, void* area, void* stream) {
+int mls_marker_prep_range(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri,
+                          int64_t n_tri, int64_t t_begin, int64_t t_end, void* x, void* area, void* stream) {
   if (!ctx) return invalid("mls_marker_prep: NULL ctx");
   if (n_tri < 0 || n_vertices < 0) return invalid("mls_marker_prep: negative size");
-  if (n_tri > 0 && (!vertices || !tri || !x || !area)) return invalid("mls_marker_prep: NULL pointer");
+  if (t_begin < 0 || t_begin > t_end || t_end > n_tri)
+    return invalid("mls_marker_prep_range: range not within [0, n_tri]");
+  if (t_end > t_begin && (!vertices || !tri || !x || !area)) return invalid("mls_marker_prep: NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
   const int slot = timer_begin(ctx, "marker_prep", s);
-  cudaError_t e = launch_prep(ctx->opt.real, vertices, n_vertices, tri, n_tri, x, area, s);
+  cudaError_t e = launch_prep(ctx->opt.real, vertices, n_vertices, tri, t_begin, t_end, n_tri, x, area, s);
   timer_end(ctx, slot, s);
   if (e != cudaSuccess) return cuda_fail(e, "mls_marker_prep");
   return MLS_OK;
+}
+
+int mls_marker_prep(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri, int64_t n_tri,
+                    void* x, void* area, void* stream) {
+  return mls_marker_prep_range(ctx, vertices, n_vertices, tri, n_tri, 0, n_tri, x, area, stream);
 }
 
 int mls_refine_markers(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri, int64_t n_tri,

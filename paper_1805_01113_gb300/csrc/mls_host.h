@@ -125,8 +125,8 @@ void timer_end(mls_ctx* ctx, int slot, cudaStream_t s);
 template <typename R> Grid<R> device_grid(const mls_ctx* ctx);
 
 // Launchers; each returns cudaGetLastError() after enqueueing.
-cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri, int64_t nt, void* x,
-                        void* area, cudaStream_t s);
+cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri, int64_t t0, int64_t t1,
+                        int64_t nt, void* x, void* area, cudaStream_t s);
 cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                           cudaStream_t s);
 cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx);

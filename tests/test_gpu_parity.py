@@ -53,6 +53,36 @@ def test_marker_prep_bit_exact(api, real):
     assert np.array_equal(ag[good], ar[good])
 
 
+@pytest.mark.parametrize("real", ["f64", "f32"])
+def test_marker_prep_in_pieces(api, real):
+    """Markers prepared body range by body range, each range after its own
+    vertices are copied (the rest of the vertex array still garbage), equal
+    the whole-array preparation bit for bit; bad ranges are refused."""
+    from paper_1805_01113_gb300 import binding as B
+    w = make_workload("c2", n=128, n_bodies=40)
+    ctx = api.Context(w.faces, w.periodic, real=real)
+    V = torch.as_tensor(w.vertices.astype(NP_DT[real]), device=DEV)
+    tri = torch.as_tensor(w.tri, device=DEV)
+    x0, a0 = ctx.marker_prep(V, tri)
+    nt = tri.shape[0]
+    Vp = torch.full_like(V, float("nan"))
+    x = torch.full((3, nt), -7.0, dtype=V.dtype, device=DEV)
+    a = torch.full((nt,), -7.0, dtype=V.dtype, device=DEV)
+    nb = len(w.body_faces) - 1
+    cuts = [int(w.body_faces[b]) for b in (0, 7, 8, 23, nb)]      # 7..8: a range of one body
+    for t0, t1 in zip(cuts[:-1], cuts[1:]):
+        v1 = int(w.tri[:t1].max()) + 1
+        Vp[:v1] = V[:v1]
+        ctx.marker_prep(Vp, tri, x, a, begin=t0, end=t1)
+        assert bool((x[:, t1:] == -7.0).all()) and bool((a[t1:] == -7.0).all())
+    ctx.marker_prep(Vp, tri, x, a, begin=nt, end=nt)                 # empty range: nothing to do
+    assert torch.equal(x, x0) and torch.equal(a, a0)
+    for t0, t1 in ((-1, 5), (6, 5), (0, nt + 1)):
+        with pytest.raises(B.MlsError) as e:
+            ctx.marker_prep(V, tri, x, a, begin=t0, end=t1)
+        assert e.value.code == B.MLS_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("method", ["exact", "fast"])
 def test_single_sphere_f64(api, method):
     """One level-4 icosphere (5120 markers) in a periodic 64^3 grid, double precision."""
