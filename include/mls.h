@@ -166,6 +166,31 @@ int mls_marker_prep_range(mls_ctx* ctx, const void* vertices, int64_t n_vertices
                           const int32_t* tri, int64_t n_tri, int64_t t_begin, int64_t t_end,
                           void* x, void* area, void* stream);
 
+/* mls_marker_prep_range of triangles [t_begin, t_end) fused with the first
+ * phase of the next build of T (Section 2: each marker's home cell and its
+ * spreading tile, as the build does first): the kernel that forms a marker
+ * also locates it, so x and area are written and not read back.  Pieces go
+ * in order: a piece with t_begin = 0 starts a new marker set (it resets T's
+ * counters and tile bins on `stream`), and every other piece must start
+ * where the previous one on T ended, with the same n_tri, x and area.  The
+ * next mls_build_transfer / mls_build_interpolate / mls_build_direct_forcing
+ * on T with M = n_tri, the same x and area, and pieces covering [0, n_tri)
+ * then skips its own locate pass; any other build locates its markers
+ * itself, as without this call.  In between, T holds scratch: the counters
+ * of mls_transfer_status count the pieces so far, and T's transfer
+ * functions must not be used (mls_interpolate, mls_spread and the like on T
+ * wait for the build).  x and area must not change before that build, and
+ * the pieces and the build run in stream order (one stream, or the caller's
+ * events between streams).
+ *   vertices, tri, x, area: as mls_marker_prep (x real[3][n_tri], area real[n_tri])
+ * Errors: MLS_ERR_CAPACITY if n_tri exceeds T's capacity; MLS_ERR_INVALID_ARG
+ * on NULL handles or pointers, a transfer of another context, negative
+ * sizes, a range outside [0, n_tri], or a piece that does not follow the
+ * previous one. */
+int mls_marker_prep_locate(mls_ctx* ctx, mls_transfer* T, const void* vertices, int64_t n_vertices,
+                           const int32_t* tri, int64_t n_tri, int64_t t_begin, int64_t t_end,
+                           void* x, void* area, void* stream);
+
 /* Build the transfer functions of M markers into T (Section 2).
  *   x     device, real[3][M] marker positions; area device, real[M] (A_l, Eq. 7)
  *   method MLS_EXACT (Eqs. 3-6), MLS_FAST (Eqs. 9-10; the first fast build

@@ -138,6 +138,22 @@ class Context:
                     "mls_marker_prep_range")
         return x, area
 
+    def marker_prep_locate(self, T, vertices, tri, x, area, begin=None, end=None, stream=None):
+        """Markers of triangles [begin, end) prepared and located for T's next build (in order, from 0)."""
+        nt = tri.shape[0]
+        _check_tensor(vertices, "vertices", self.real_t)
+        _check_tensor(tri, "tri", torch.int32, (nt, 3))
+        if vertices.dim() != 2 or vertices.shape[1] != 3:
+            raise ValueError("vertices must be (n_vertices, 3)")
+        _check_tensor(x, "x", self.real_t, (3, nt))
+        _check_tensor(area, "area", self.real_t, (nt,))
+        t0 = 0 if begin is None else int(begin)
+        t1 = nt if end is None else int(end)
+        B.check(self.lib.mls_marker_prep_locate(self.handle, T.handle, _ptr(vertices), vertices.shape[0], _ptr(tri),
+                                                nt, t0, t1, _ptr(x), _ptr(area), _stream(stream)),
+                "mls_marker_prep_locate")
+        return x, area
+
     def build_transfer(self, T, x, area, method="exact", stream=None):
         M = x.shape[1]
         _check_tensor(x, "x", self.real_t, (3, M))

@@ -70,6 +70,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p]),
     "mls_marker_prep_range": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
                                         C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mls_marker_prep_locate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                         C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mls_build_transfer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                      C.c_void_p]),
     "mls_interpolate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

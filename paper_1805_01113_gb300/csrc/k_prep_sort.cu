@@ -52,30 +52,80 @@ cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri,
 constexpr int kLocatePer = 4;
 inline int locate_per(int64_t M) { return M >= (int64_t)kLocatePer * 152 * 2048 ? kLocatePer : 1; }
 
-// Home cell of every marker, its spreading-tile bin, and its rank inside the
-// bin (warp-aggregated atomic counter per bin).  Dropped markers go to the
-// last bin and are counted in status[0] (all) and status[1] (non-finite).
-template <typename R, int PER>
+// Triangles whose markers the locate kernel forms itself (the preparation
+// fused into it): vertices, their count, the triangles, and where the
+// markers' positions and areas go.
+template <typename R>
+struct PrepSource {
+  const R* V;
+  int64_t nv;
+  const int32_t* tri;
+  R* x;
+  R* area;
+};
+
+// Home cell of markers [j0, j1) of M, their spreading-tile bins, and their
+// ranks inside the bins (warp-aggregated atomic counter per bin).  Dropped
+// markers go to the last bin and are counted in status[0] (all) and
+// status[1] (non-finite).  With PREP the markers are first formed from their
+// triangles as by k_prep (same operations, same NaN rule) and stored.
+template <typename R, int PER, bool PREP>
 __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R* __restrict__ x,
-                                                   const R* __restrict__ area, int64_t M,
-                                                   int32_t* __restrict__ key, int32_t* __restrict__ rank,
-                                                   int32_t* __restrict__ counts,
+                                                   const R* __restrict__ area, int64_t M, int64_t j0, int64_t j1,
+                                                   PrepSource<R> src, int32_t* __restrict__ key,
+                                                   int32_t* __restrict__ rank, int32_t* __restrict__ counts,
                                                    unsigned long long* __restrict__ status,
                                                    int32_t* __restrict__ sub) {
   // A warp takes PER rounds of 32 consecutive markers; every round's
   // loads, then every round's bin counter update, are issued before any
   // result is waited for.
   const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * PER);
+  const int64_t w0 = j0 + ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * PER);
   R p[PER][3], ar[PER];
+  if constexpr (PREP) {
+    using O = Ops<R>;
+    int64_t iv[PER][3];
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int64_t j = w0 + r * 32 + lane;
-    if (j < M) {
-      p[r][0] = x[j];
-      p[r][1] = x[M + j];
-      p[r][2] = x[2 * M + j];
-      ar[r] = area[j];
+    for (int r = 0; r < PER; ++r) {
+      const int64_t j = w0 + r * 32 + lane;
+      if (j < j1) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) iv[r][q] = src.tri[3 * j + q];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int64_t j = w0 + r * 32 + lane;
+      if (j < j1) {
+        const int64_t i0 = iv[r][0], i1 = iv[r][1], i2 = iv[r][2];
+        if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= src.nv || i1 >= src.nv || i2 >= src.nv) {
+          p[r][0] = p[r][1] = p[r][2] = ar[r] = O::nan_();
+        } else {
+          R va[3], vb[3], vc[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            va[d] = src.V[3 * i0 + d];
+            vb[d] = src.V[3 * i1 + d];
+            vc[d] = src.V[3 * i2 + d];
+          }
+          triangle_marker(va, vb, vc, p[r], ar[r]);
+        }
+        src.x[j] = p[r][0];
+        src.x[M + j] = p[r][1];
+        src.x[2 * M + j] = p[r][2];
+        src.area[j] = ar[r];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int64_t j = w0 + r * 32 + lane;
+      if (j < j1) {
+        p[r][0] = x[j];
+        p[r][1] = x[M + j];
+        p[r][2] = x[2 * M + j];
+        ar[r] = area[j];
+      }
     }
   }
   int k[PER], cell[PER];
@@ -86,7 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R*
     const int64_t j = w0 + r * 32 + lane;
     k[r] = -1;   // no marker: a group of its own that counts nothing
     cell[r] = 0;
-    if (j < M) {
+    if (j < j1) {
       const bool finite = isfinite(p[r][0]) && isfinite(p[r][1]) && isfinite(p[r][2]) && isfinite(ar[r]);
       bool ok = finite;
       int h[3];
@@ -113,7 +163,7 @@ __global__ void __launch_bounds__(kBlock) k_locate(Grid<R> g, Tiles tl, const R*
   for (int r = 0; r < PER; ++r) {
     const int64_t j = w0 + r * 32 + lane;
     const int b = __shfl_sync(0xffffffffu, base[r], __ffs(peers[r]) - 1);
-    if (j < M) {
+    if (j < j1) {
       key[j] = k[r];
       rank[j] = b + __popc(peers[r] & ((1u << lane) - 1u));
       if (sub && k[r] != tl.nbins - 1) sub[j] = cell[r];
@@ -130,19 +180,38 @@ bool tile_sort_on(const mls_ctx* ctx) {
   return ctx->tiles.l[0] + ctx->tiles.l[1] + ctx->tiles.l[2] <= kSortCellsLog2;
 }
 
+template <typename R>
+static void locate_range(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
+                         int64_t j0, int64_t j1, PrepSource<R> src, bool prep, cudaStream_t s) {
+  const int64_t n = j1 - j0;
+  const int per = locate_per(n);
+  const unsigned grid = (unsigned)((n + kBlock * per - 1) / (kBlock * per));
+  int32_t* sub = tile_sort_on(ctx) ? reinterpret_cast<int32_t*>(T->phi) : nullptr;
+  auto kern = prep ? (per == kLocatePer ? k_locate<R, kLocatePer, true> : k_locate<R, 1, true>)
+                   : (per == kLocatePer ? k_locate<R, kLocatePer, false> : k_locate<R, 1, false>);
+  kern<<<grid, kBlock, 0, s>>>(device_grid<R>(ctx), ctx->tiles, (const R*)x, (const R*)area, M, j0, j1, src, T->key,
+                               T->rank, T->counts, T->status, sub);
+}
+
 cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                           cudaStream_t s) {
-  const int per = locate_per(M);
-  const unsigned grid = (unsigned)((M + kBlock * per - 1) / (kBlock * per));
-  int32_t* sub = tile_sort_on(ctx) ? reinterpret_cast<int32_t*>(T->phi) : nullptr;
+  if (M <= 0) return cudaSuccess;
   if (ctx->opt.real == MLS_F64)
-    (per == kLocatePer ? k_locate<double, kLocatePer> : k_locate<double, 1>)<<<grid, kBlock, 0, s>>>(
-        device_grid<double>(ctx), ctx->tiles, (const double*)x, (const double*)area, M, T->key, T->rank, T->counts,
-        T->status, sub);
+    locate_range<double>(ctx, T, x, area, M, 0, M, PrepSource<double>{}, false, s);
   else
-    (per == kLocatePer ? k_locate<float, kLocatePer> : k_locate<float, 1>)<<<grid, kBlock, 0, s>>>(
-        device_grid<float>(ctx), ctx->tiles, (const float*)x, (const float*)area, M, T->key, T->rank, T->counts,
-        T->status, sub);
+    locate_range<float>(ctx, T, x, area, M, 0, M, PrepSource<float>{}, false, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_locate(const mls_ctx* ctx, mls_transfer* T, const void* V, int64_t nv, const int32_t* tri,
+                               int64_t nt, int64_t t0, int64_t t1, void* x, void* area, cudaStream_t s) {
+  if (t1 <= t0) return cudaSuccess;
+  if (ctx->opt.real == MLS_F64)
+    locate_range<double>(ctx, T, nullptr, nullptr, nt, t0, t1,
+                         PrepSource<double>{(const double*)V, nv, tri, (double*)x, (double*)area}, true, s);
+  else
+    locate_range<float>(ctx, T, nullptr, nullptr, nt, t0, t1,
+                        PrepSource<float>{(const float*)V, nv, tri, (float*)x, (float*)area}, true, s);
   return cudaGetLastError();
 }
 

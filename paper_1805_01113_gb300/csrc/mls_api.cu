@@ -315,6 +315,7 @@ int mls_transfer_create(mls_ctx* ctx, int64_t capacity, mls_transfer** out) {
   T->cap = capacity;
   T->M = 0;
   T->method = MLS_EXACT;
+  T->pre_M = -1;
   const size_t rs = ctx->opt.real == MLS_F64 ? sizeof(double) : sizeof(float);
   const int nbins = ctx->tiles.nbins;
   T->ntiles = (nbins + kScanTile - 1) / kScanTile;
@@ -364,6 +365,50 @@ int mls_marker_prep_range(mls_ctx* ctx, const void* vertices, int64_t n_vertices
 int mls_marker_prep(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri, int64_t n_tri,
                     void* x, void* area, void* stream) {
   return mls_marker_prep_range(ctx, vertices, n_vertices, tri, n_tri, 0, n_tri, x, area, stream);
+}
+
+int mls_marker_prep_locate(mls_ctx* ctx, mls_transfer* T, const void* vertices, int64_t n_vertices,
+                           const int32_t* tri, int64_t n_tri, int64_t t_begin, int64_t t_end, void* x, void* area,
+                           void* stream) {
+  if (!ctx || !T) return invalid("mls_marker_prep_locate: NULL handle");
+  if (T->ctx != ctx) return invalid("mls_marker_prep_locate: transfer belongs to another context");
+  if (n_tri < 0 || n_vertices < 0) return invalid("mls_marker_prep_locate: negative size");
+  if (n_tri > T->cap) {
+    set_error("mls_marker_prep_locate: n_tri exceeds the transfer capacity");
+    return MLS_ERR_CAPACITY;
+  }
+  if (t_begin < 0 || t_begin > t_end || t_end > n_tri)
+    return invalid("mls_marker_prep_locate: range not within [0, n_tri]");
+  if (n_tri > 0 && (!vertices || !tri || !x || !area)) return invalid("mls_marker_prep_locate: NULL pointer");
+  if (t_begin != 0 &&
+      !(T->pre_M == n_tri && T->pre_done == t_begin && T->pre_x == x && T->pre_area == area))
+    return invalid("mls_marker_prep_locate: a piece must start at triangle 0 or where the previous piece on this "
+                   "transfer ended, with the same n_tri, x and area");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (t_begin == 0) {
+    // A new set of markers: the counters and tile bins of the next build start from zero.
+    T->pre_M = -1;
+    if ((e = cudaMemsetAsync(T->status, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+      return cuda_fail(e, "mls_marker_prep_locate: status reset");
+    const int slot = timer_begin(ctx, "bin_reset", s);
+    e = cudaMemsetAsync(T->counts, 0, (size_t)ctx->tiles.nbins * 4, s);
+    timer_end(ctx, slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mls_marker_prep_locate: bin reset");
+    T->pre_x = x;
+    T->pre_area = area;
+    T->pre_M = n_tri;
+    T->pre_done = 0;
+  }
+  const int slot = timer_begin(ctx, "prep_locate", s);
+  e = launch_prep_locate(ctx, T, vertices, n_vertices, tri, n_tri, t_begin, t_end, x, area, s);
+  timer_end(ctx, slot, s);
+  if (e != cudaSuccess) {
+    T->pre_M = -1;
+    return cuda_fail(e, "mls_marker_prep_locate");
+  }
+  T->pre_done = t_end;
+  return MLS_OK;
 }
 
 int mls_refine_markers(mls_ctx* ctx, const void* vertices, int64_t n_vertices, const int32_t* tri, int64_t n_tri,
@@ -450,18 +495,25 @@ static int build_impl(mls_ctx* ctx, mls_transfer* T, const void* x, const void* 
   }
   T->M = M;
   T->method = method;
+  // Markers that mls_marker_prep_locate has already located, all of them, in
+  // these arrays: the counters, bins and tile keys are in place.
+  const bool located = M > 0 && T->pre_M == M && T->pre_done == M && T->pre_x == x && T->pre_area == area;
+  T->pre_M = -1;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(T->status, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
-    return cuda_fail(e, "mls_build_transfer: status reset");
-  if (M == 0) return MLS_OK;
-  int slot = timer_begin(ctx, "bin_reset", s);
-  e = cudaMemsetAsync(T->counts, 0, (size_t)ctx->tiles.nbins * 4, s);
-  timer_end(ctx, slot, s);
-  if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: bin reset");
-  slot = timer_begin(ctx, "locate", s);
-  e = launch_locate(ctx, T, x, area, M, s);
-  timer_end(ctx, slot, s);
-  if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: locate");
+  int slot = -1;
+  if (!located) {
+    if ((e = cudaMemsetAsync(T->status, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+      return cuda_fail(e, "mls_build_transfer: status reset");
+    if (M == 0) return MLS_OK;
+    slot = timer_begin(ctx, "bin_reset", s);
+    e = cudaMemsetAsync(T->counts, 0, (size_t)ctx->tiles.nbins * 4, s);
+    timer_end(ctx, slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: bin reset");
+    slot = timer_begin(ctx, "locate", s);
+    e = launch_locate(ctx, T, x, area, M, s);
+    timer_end(ctx, slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: locate");
+  }
   e = launch_scan(T, ctx->tiles.nbins, s, ctx);
   if (e != cudaSuccess) return cuda_fail(e, "mls_build_transfer: scan");
   slot = timer_begin(ctx, "scatter", s);

@@ -79,6 +79,13 @@ struct mls_transfer {
   int32_t* tile_sums;  // [2 * ntiles]: per scan tile, marker sums then non-empty-bin sums
   int ntiles;        // scan tiles over the bins
   unsigned long long* status;  // [4] dropped, nonfinite, refined_fp64, spare
+  // Markers already prepared and located for the next build, piece by piece
+  // (mls_marker_prep_locate): their arrays, count and the end of the pieces
+  // so far.  pre_M < 0: none.
+  const void* pre_x;
+  const void* pre_area;
+  int64_t pre_M;
+  int64_t pre_done;
 };
 
 namespace mls {
@@ -129,6 +136,8 @@ cudaError_t launch_prep(int real, const void* V, int64_t nv, const int32_t* tri,
                         int64_t nt, void* x, void* area, cudaStream_t s);
 cudaError_t launch_locate(const mls_ctx* ctx, mls_transfer* T, const void* x, const void* area, int64_t M,
                           cudaStream_t s);
+cudaError_t launch_prep_locate(const mls_ctx* ctx, mls_transfer* T, const void* V, int64_t nv, const int32_t* tri,
+                               int64_t nt, int64_t t0, int64_t t1, void* x, void* area, cudaStream_t s);
 cudaError_t launch_scan(mls_transfer* T, int nbins, cudaStream_t s, mls_ctx* ctx);
 cudaError_t launch_scatter(const mls_ctx* ctx, mls_transfer* T, int64_t M, cudaStream_t s);
 bool tile_sort_on(const mls_ctx* ctx);
