@@ -367,8 +367,7 @@ def run_ours(a, rank, world, local):
     F_df = torch.empty((3, M), dtype=tdt, device=dev)
 
     def step(method):
-        # markers formed and located in one kernel; the build then skips its locate pass
-        ctx.marker_prep_locate(T, V, tri, x, area)
+        ctx.marker_prep(V, tri, x, area)
         if method == "direct_forcing":
             ctx.build_transfer(T, x, area, "exact")
             ctx.direct_forcing(T, u, Vb0, DT, f, F=F_df, U=U)
@@ -507,7 +506,7 @@ def run_ours(a, rank, world, local):
     bd = algorithmic_bytes("direct_forcing", rs, u_cells, vpm) * M
     others["direct_forcing"] = {
         "value": M * world / (statistics.mean(ms_d) / 1e3), "ms_per_step": statistics.mean(ms_d),
-        "step": "marker_prep_locate + build_transfer (exact) + direct_forcing (V_b = 0, dt = 1e-3)",
+        "step": "marker_prep + build_transfer (exact) + direct_forcing (V_b = 0, dt = 1e-3)",
         "kernel_ms": kd, "algorithmic_bytes_per_launch": bd, "achieved_gbs": bd / (kd / 1e3) / 1e9,
         "frac": bd / (kd / 1e3) / 1e9 / pk["hbm_gbs"],
         "separate_interp_spread_ms": per_launch.get("interp", 0.0) + per_launch.get("spread", 0.0)}
@@ -516,7 +515,7 @@ def run_ours(a, rank, world, local):
     _, kt_bd = timed("build_direct_forcing", 3, 1, True)
     others["build_direct_forcing"] = {
         "value": M * world / (statistics.mean(ms_bd) / 1e3), "ms_per_step": statistics.mean(ms_bd),
-        "step": "marker_prep_locate + build_direct_forcing (exact; U and F = (V_b - U)/dt in the build kernel, then spread)",
+        "step": "marker_prep + build_direct_forcing (exact; U and F = (V_b - U)/dt in the build kernel, then spread)",
         "kernels_ms": {k: round(n_t[1] / n_t[0], 5) for k, n_t in kt_bd.items() if n_t[0]}}
     # the same exact step as three separate calls (build_transfer, interpolate, spread)
     if a.method == "exact":
@@ -525,7 +524,7 @@ def run_ours(a, rank, world, local):
         kb = {k: n_t[1] / n_t[0] for k, n_t in kt_b.items() if n_t[0]}
         others["exact_separate"] = {
             "value": M * world / (statistics.mean(ms_b) / 1e3), "ms_per_step": statistics.mean(ms_b),
-            "step": "marker_prep_locate + build_transfer (exact) + interpolate + spread",
+            "step": "marker_prep + build_transfer (exact) + interpolate + spread",
             "build_ms": kb.get("build_exact"), "interp_ms": kb.get("interp"),
             "fused_build_interp_ms": per_launch.get("build_exact_interp")}
     # velocity gradient at the markers from the exact-MLS shape-function derivatives
@@ -813,7 +812,7 @@ def run_ours(a, rank, world, local):
             Tb = cb.transfer(M)
 
             def step_b():
-                cb.marker_prep_locate(Tb, V, tri, x, area)
+                cb.marker_prep(V, tri, x, area)
                 cb.build_interpolate(Tb, x, area, ub, U, method="exact")
                 cb.spread(Tb, F, fb)
 
@@ -884,9 +883,9 @@ def run_ours(a, rank, world, local):
                    f"{a.workload} variant: {len(w.body_faces) - 1} bodies, {w.n[0]}x{w.n[1]}x{w.n[2]} grid",
                    "markers_per_gpu": M, "method": a.method, "grid": list(w.n),
                    "l2": "flushed by a 256 MiB write before every timed step",
-                   "step": ("marker_prep_locate + build_interpolate (build and interpolation in one call, the "
+                   "step": ("marker_prep + build_interpolate (build and interpolation in one call, the "
                             "interpolation inside the exact build kernel) + spread" if a.method == "exact" else
-                            "marker_prep_locate + build_interpolate (build_transfer + interpolate in turn) + spread"),
+                            "marker_prep + build_interpolate (build_transfer + interpolate in turn) + spread"),
                    "graph": graph_state["use"], "graph_error": graph_state["error"], "tiles_log2": list(tiles),
                    "autotune_ms": {str(k): round(v, 4) for k, v in tune_ms.items()} if tune_ms else None,
                    "touched_cells_per_marker": round(u_cells, 4)},
